@@ -1,0 +1,372 @@
+/*
+ * Seeded synthetic graph generators and the CSR builder.
+ *
+ * This file produces INPUTS only: undirected graphs in CSR form and source
+ * lists.  It holds none of the betweenness-centrality arithmetic, so both the
+ * CUDA library and the CPU oracle may consume what it writes.
+ *
+ * Graph conventions (Sec. V, "directed graphs were converted to undirected"):
+ * every graph is returned symmetric, with no self-loops, no duplicate entries
+ * and rows sorted ascending; row_ptr and col are int32 (nnz < 2^31).
+ *
+ * Randomness: one counter-based generator, SplitMix64 (Steele, Lea, Flood,
+ * "Fast splittable pseudorandom number generators", OOPSLA 2014): value i of
+ * stream (seed, id) is the SplitMix64 output mixer applied to
+ * key + (i + 1) * 0x9E3779B97F4A7C15.  Only integer arithmetic is used, so the
+ * same seed gives the same bytes on x86-64 and AArch64.
+ *
+ * Memory returned in gg_csr / gg_i32 is malloc'd here; release with gg_free_*.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define GG_GOLDEN 0x9E3779B97F4A7C15ULL
+
+static inline uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Key of stream `id` under `seed`. */
+static inline uint64_t gg_key(uint64_t seed, uint64_t id) {
+    return sm64_mix(sm64_mix(seed + GG_GOLDEN) ^ (id * 0xD1B54A32D192ED03ULL + 1));
+}
+
+static inline uint64_t gg_at(uint64_t key, uint64_t i) {
+    return sm64_mix(key + (i + 1) * GG_GOLDEN);
+}
+
+uint64_t gg_rng(uint64_t seed, uint64_t id, uint64_t i) { return gg_at(gg_key(seed, id), i); }
+
+/* Uniform integer in [0, range) by the multiply-high method (Lemire 2019,
+ * without the rejection step: bias below range / 2^64). */
+static inline uint64_t gg_bounded(uint64_t r, uint64_t range) {
+    return (uint64_t)(((__uint128_t)r * (__uint128_t)range) >> 64);
+}
+
+enum { ST_ER = 1, ST_RMAT = 2, ST_PERM = 3, ST_GRID = 4, ST_SRC = 5 };
+
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    int32_t *row_ptr; /* n + 1 */
+    int32_t *col;     /* nnz */
+} gg_csr;
+
+void gg_free_csr(gg_csr *g) {
+    if (!g) return;
+    free(g->row_ptr);
+    free(g->col);
+    g->row_ptr = NULL;
+    g->col = NULL;
+}
+void gg_free_ptr(void *p) { free(p); }
+
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Edge list -> symmetric, sorted, deduplicated, loop-free CSR.
+ * Returns 0, or -1 on a bad vertex id / allocation failure / nnz >= 2^31. */
+int gg_from_edges(int32_t n, int64_t m, const int32_t *u, const int32_t *v, gg_csr *out) {
+    memset(out, 0, sizeof(*out));
+    if (n < 0 || m < 0) return -1;
+    int64_t *deg = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!deg) return -1;
+    for (int64_t e = 0; e < m; ++e) {
+        int32_t a = u[e], b = v[e];
+        if (a < 0 || b < 0 || a >= n || b >= n) { free(deg); return -1; }
+        if (a == b) continue;
+        deg[a]++;
+        deg[b]++;
+    }
+    int64_t *off = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+    if (!off) { free(deg); return -1; }
+    off[0] = 0;
+    for (int32_t i = 0; i < n; ++i) off[i + 1] = off[i] + deg[i];
+    int64_t total = off[n];
+    int32_t *tmp = (int32_t *)malloc((size_t)(total > 0 ? total : 1) * sizeof(int32_t));
+    if (!tmp) { free(deg); free(off); return -1; }
+    memset(deg, 0, ((size_t)n + 1) * sizeof(int64_t));
+    for (int64_t e = 0; e < m; ++e) {
+        int32_t a = u[e], b = v[e];
+        if (a == b) continue;
+        tmp[off[a] + deg[a]++] = b;
+        tmp[off[b] + deg[b]++] = a;
+    }
+    /* sort + dedup each row in place, recording the kept length in deg[] */
+    int64_t nnz = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t *row = tmp + off[i];
+        int64_t len = deg[i];
+        if (len > 1) qsort(row, (size_t)len, sizeof(int32_t), cmp_i32);
+        int64_t k = 0;
+        for (int64_t j = 0; j < len; ++j)
+            if (k == 0 || row[j] != row[k - 1]) row[k++] = row[j];
+        deg[i] = k;
+        nnz += k;
+    }
+    if (nnz >= ((int64_t)1 << 31)) { free(deg); free(off); free(tmp); return -1; }
+    out->n = n;
+    out->nnz = nnz;
+    out->row_ptr = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    out->col = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    if (!out->row_ptr || !out->col) { gg_free_csr(out); free(deg); free(off); free(tmp); return -1; }
+    int64_t p = 0;
+    out->row_ptr[0] = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        memcpy(out->col + p, tmp + off[i], (size_t)deg[i] * sizeof(int32_t));
+        p += deg[i];
+        out->row_ptr[i + 1] = (int32_t)p;
+    }
+    free(deg);
+    free(off);
+    free(tmp);
+    return 0;
+}
+
+/* Erdos-Renyi G(n, p): each of the n(n-1)/2 pairs is an edge iff its draw is
+ * below thr = floor(p * 2^64).  O(n^2) draws, meant for n up to ~10^5. */
+int gg_er(int32_t n, uint64_t thr, uint64_t seed, gg_csr *out) {
+    uint64_t key = gg_key(seed, ST_ER);
+    int64_t cap = 1024, m = 0;
+    int32_t *eu = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    int32_t *ev = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    if (!eu || !ev) { free(eu); free(ev); return -1; }
+    uint64_t idx = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t j = i + 1; j < n; ++j, ++idx) {
+            if (gg_at(key, idx) < thr) {
+                if (m == cap) {
+                    cap *= 2;
+                    int32_t *nu = (int32_t *)realloc(eu, (size_t)cap * sizeof(int32_t));
+                    int32_t *nv = (int32_t *)realloc(ev, (size_t)cap * sizeof(int32_t));
+                    if (!nu || !nv) { free(nu ? nu : eu); free(nv ? nv : ev); return -1; }
+                    eu = nu;
+                    ev = nv;
+                }
+                eu[m] = i;
+                ev[m] = j;
+                ++m;
+            }
+        }
+    }
+    int rc = gg_from_edges(n, m, eu, ev, out);
+    free(eu);
+    free(ev);
+    return rc;
+}
+
+/* Seeded uniform permutation of [0, n) (Fisher-Yates, Durstenfeld form). */
+int gg_permutation(int32_t n, uint64_t seed, uint64_t stream, int32_t *perm) {
+    uint64_t key = gg_key(seed, stream);
+    for (int32_t i = 0; i < n; ++i) perm[i] = i;
+    for (int32_t i = n - 1; i > 0; --i) {
+        int32_t j = (int32_t)gg_bounded(gg_at(key, (uint64_t)i), (uint64_t)i + 1);
+        int32_t t = perm[i];
+        perm[i] = perm[j];
+        perm[j] = t;
+    }
+    return 0;
+}
+
+/* R-MAT (Chakrabarti, Zhan, Faloutsos, SDM 2004) without noise: edge e picks
+ * one quadrant per bit with probabilities a, b, c, d; thresholds are given as
+ * 32-bit fixed point (ta = floor(a 2^32), tab = floor((a+b) 2^32), ...).
+ * permute != 0 relabels vertices by a seeded permutation so that hubs are
+ * spread over the id range. */
+int gg_rmat(int32_t scale, int32_t edge_factor, uint32_t ta, uint32_t tab, uint32_t tabc,
+            uint64_t seed, int32_t permute, gg_csr *out) {
+    memset(out, 0, sizeof(*out));
+    if (scale < 1 || scale > 30 || edge_factor < 1) return -1;
+    int32_t n = (int32_t)1 << scale;
+    int64_t m = (int64_t)edge_factor * n;
+    int32_t *eu = (int32_t *)malloc((size_t)m * sizeof(int32_t));
+    int32_t *ev = (int32_t *)malloc((size_t)m * sizeof(int32_t));
+    int32_t *perm = permute ? (int32_t *)malloc((size_t)n * sizeof(int32_t)) : NULL;
+    if (!eu || !ev || (permute && !perm)) { free(eu); free(ev); free(perm); return -1; }
+    uint64_t key = gg_key(seed, ST_RMAT);
+    int64_t draws_per_edge = (scale + 1) / 2;
+    for (int64_t e = 0; e < m; ++e) {
+        uint32_t a = 0, b = 0;
+        for (int32_t lvl = 0; lvl < scale; ++lvl) {
+            uint64_t r64 = gg_at(key, (uint64_t)(e * draws_per_edge + lvl / 2));
+            uint32_t r = (lvl & 1) ? (uint32_t)(r64 >> 32) : (uint32_t)r64;
+            uint32_t bu, bv;
+            if (r < ta) { bu = 0; bv = 0; }
+            else if (r < tab) { bu = 0; bv = 1; }
+            else if (r < tabc) { bu = 1; bv = 0; }
+            else { bu = 1; bv = 1; }
+            a = (a << 1) | bu;
+            b = (b << 1) | bv;
+        }
+        eu[e] = (int32_t)a;
+        ev[e] = (int32_t)b;
+    }
+    if (permute) {
+        gg_permutation(n, seed, ST_PERM, perm);
+        for (int64_t e = 0; e < m; ++e) {
+            eu[e] = perm[eu[e]];
+            ev[e] = perm[ev[e]];
+        }
+    }
+    int rc = gg_from_edges(n, m, eu, ev, out);
+    free(eu);
+    free(ev);
+    free(perm);
+    return rc;
+}
+
+/* Connected components by BFS; comp[v] = component index in discovery order
+ * (by smallest vertex id).  Returns the number of components. */
+static int32_t components(const gg_csr *g, int32_t *comp, int32_t *queue) {
+    for (int32_t v = 0; v < g->n; ++v) comp[v] = -1;
+    int32_t nc = 0;
+    for (int32_t s = 0; s < g->n; ++s) {
+        if (comp[s] >= 0) continue;
+        int32_t head = 0, tail = 0;
+        queue[tail++] = s;
+        comp[s] = nc;
+        while (head < tail) {
+            int32_t x = queue[head++];
+            for (int32_t p = g->row_ptr[x]; p < g->row_ptr[x + 1]; ++p) {
+                int32_t y = g->col[p];
+                if (comp[y] < 0) { comp[y] = nc; queue[tail++] = y; }
+            }
+        }
+        ++nc;
+    }
+    return nc;
+}
+
+/* Largest connected component (ties: the one holding the smallest id), with
+ * vertices relabelled compactly in increasing old-id order. old_id (optional,
+ * n entries) receives the old id of each kept vertex. */
+int gg_lcc(const gg_csr *g, gg_csr *out, int32_t *old_id) {
+    memset(out, 0, sizeof(*out));
+    int32_t n = g->n;
+    if (n == 0) {
+        out->row_ptr = (int32_t *)calloc(1, sizeof(int32_t));
+        out->col = (int32_t *)malloc(sizeof(int32_t));
+        return out->row_ptr && out->col ? 0 : -1;
+    }
+    int32_t *comp = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!comp || !queue) { free(comp); free(queue); return -1; }
+    int32_t nc = components(g, comp, queue);
+    int64_t *size = (int64_t *)calloc((size_t)nc, sizeof(int64_t));
+    if (!size) { free(comp); free(queue); return -1; }
+    for (int32_t v = 0; v < n; ++v) size[comp[v]]++;
+    int32_t best = 0;
+    for (int32_t c = 1; c < nc; ++c)
+        if (size[c] > size[best]) best = c;
+    int32_t *newid = queue; /* reuse */
+    int32_t k = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        if (comp[v] == best) {
+            if (old_id) old_id[k] = v;
+            newid[v] = k++;
+        } else {
+            newid[v] = -1;
+        }
+    }
+    int64_t nnz = 0;
+    for (int32_t v = 0; v < n; ++v)
+        if (newid[v] >= 0) nnz += g->row_ptr[v + 1] - g->row_ptr[v];
+    out->n = k;
+    out->nnz = nnz;
+    out->row_ptr = (int32_t *)malloc(((size_t)k + 1) * sizeof(int32_t));
+    out->col = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    if (!out->row_ptr || !out->col) { gg_free_csr(out); free(comp); free(queue); free(size); return -1; }
+    int64_t p = 0;
+    out->row_ptr[0] = 0;
+    for (int32_t v = 0, r = 0; v < n; ++v) {
+        if (newid[v] < 0) continue;
+        /* relabelling is monotone, so each row stays sorted */
+        for (int32_t q = g->row_ptr[v]; q < g->row_ptr[v + 1]; ++q) out->col[p++] = newid[g->col[q]];
+        out->row_ptr[++r] = (int32_t)p;
+    }
+    free(comp);
+    free(queue);
+    free(size);
+    return 0;
+}
+
+/* side x side 4-neighbour grid; remove_count edges removed uniformly without
+ * replacement (partial Fisher-Yates over edge indices); keep_lcc keeps the
+ * largest component, relabelled in row-major order.  Vertex (i, j) = i*side+j
+ * before relabelling.  Edge index: horizontal (i,j)-(i,j+1) -> i*(side-1)+j,
+ * vertical (i,j)-(i+1,j) -> side*(side-1) + i*side + j. */
+int gg_grid(int32_t side, int64_t remove_count, uint64_t seed, int32_t keep_lcc, gg_csr *out) {
+    memset(out, 0, sizeof(*out));
+    if (side < 1 || (int64_t)side * side >= ((int64_t)1 << 31)) return -1;
+    int64_t H = (int64_t)side * (side - 1);
+    int64_t E = 2 * H;
+    if (remove_count < 0 || remove_count > E) return -1;
+    int64_t *idx = (int64_t *)malloc((size_t)(E > 0 ? E : 1) * sizeof(int64_t));
+    uint8_t *removed = (uint8_t *)calloc((size_t)(E > 0 ? E : 1), 1);
+    if (!idx || !removed) { free(idx); free(removed); return -1; }
+    for (int64_t e = 0; e < E; ++e) idx[e] = e;
+    uint64_t key = gg_key(seed, ST_GRID);
+    for (int64_t i = 0; i < remove_count; ++i) {
+        int64_t j = i + (int64_t)gg_bounded(gg_at(key, (uint64_t)i), (uint64_t)(E - i));
+        int64_t t = idx[i];
+        idx[i] = idx[j];
+        idx[j] = t;
+        removed[idx[i]] = 1;
+    }
+    int64_t m = E - remove_count;
+    int32_t *eu = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    int32_t *ev = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    if (!eu || !ev) { free(idx); free(removed); free(eu); free(ev); return -1; }
+    int64_t q = 0;
+    for (int64_t e = 0; e < E; ++e) {
+        if (removed[e]) continue;
+        int32_t a, b;
+        if (e < H) {
+            int32_t i = (int32_t)(e / (side - 1)), j = (int32_t)(e % (side - 1));
+            a = i * side + j;
+            b = a + 1;
+        } else {
+            int64_t f = e - H;
+            int32_t i = (int32_t)(f / side), j = (int32_t)(f % side);
+            a = i * side + j;
+            b = a + side;
+        }
+        eu[q] = a;
+        ev[q] = b;
+        ++q;
+    }
+    free(idx);
+    free(removed);
+    gg_csr full;
+    int rc = gg_from_edges(side * side, m, eu, ev, &full);
+    free(eu);
+    free(ev);
+    if (rc) return rc;
+    if (!keep_lcc) { *out = full; return 0; }
+    rc = gg_lcc(&full, out, NULL);
+    gg_free_csr(&full);
+    return rc;
+}
+
+/* k distinct sources drawn uniformly from [0, n) (partial Fisher-Yates). */
+int gg_sample_sources(int32_t n, int64_t k, uint64_t seed, int32_t *out) {
+    if (k < 0 || k > n) return -1;
+    int32_t *pool = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!pool) return -1;
+    for (int32_t i = 0; i < n; ++i) pool[i] = i;
+    uint64_t key = gg_key(seed, ST_SRC);
+    for (int64_t i = 0; i < k; ++i) {
+        int64_t j = i + (int64_t)gg_bounded(gg_at(key, (uint64_t)i), (uint64_t)(n - i));
+        int32_t t = pool[i];
+        pool[i] = pool[j];
+        pool[j] = t;
+        out[i] = pool[i];
+    }
+    free(pool);
+    return 0;
+}
