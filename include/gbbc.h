@@ -1,0 +1,181 @@
+/*
+ * gbbc.h - C ABI of libgbbc.so: exact Brandes betweenness centrality on one
+ * GB300 (sm_103a), unweighted undirected graphs, the whole graph in HBM.
+ *
+ * The problem statement follows Sec. II of the paper: the input is a graph
+ * with N vertices and M edges and a set of sources (Algorithm 1's input);
+ * the output is BC[v] = sum over sources s != v of delta_s(v) (Eq. 1, Eq. 2).
+ * BC counts ordered pairs (s, t): no factor 1/2 for undirected graphs, and no
+ * rescaling when only k < n sources are used.
+ *
+ * Conventions for every call
+ *  - Every call returns a gbbc_status; nothing throws across this boundary.
+ *    Output buffers are left untouched when the status is not GBBC_OK.
+ *  - Pointers may point to host memory or to CUDA device memory of the
+ *    current device; the library tells them apart with
+ *    cudaPointerGetAttributes.  The caller owns all buffers it passes in;
+ *    the library copies inputs before returning and owns all device memory
+ *    it allocates (released by bc_graph_destroy).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued on it; a call may synchronize it internally.  One handle must
+ *    not be used from two host threads at once, and calls on one handle are
+ *    ordered on the stream given to them.
+ *  - Device-side failures (queue capacity, sigma width, a bounded device
+ *    wait that gave up) are detected by the library and reported as status
+ *    codes; no kernel traps.
+ *
+ * Graph format: CSR with int32 row_ptr[n+1] and int32 col[nnz]; the graph
+ * must be symmetric (undirected), with no self-loops and no duplicate
+ * entries (a duplicate would count a path twice); rows need not be sorted
+ * unless validation is on.  nnz < 2^31.
+ */
+#ifndef GBBC_H
+#define GBBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbbc_graph gbbc_graph; /* opaque handle */
+
+typedef enum gbbc_status {
+    GBBC_OK = 0,
+    GBBC_ERR_INVALID = 1,  /* bad argument or graph (see bc_last_error_detail) */
+    GBBC_ERR_OOM = 2,      /* device allocation failed or mem_limit_bytes hit */
+    GBBC_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+    GBBC_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+    GBBC_ERR_CAPACITY = 5, /* an internal queue or the sigma format overflowed */
+    GBBC_ERR_STATE = 6     /* call not valid in the handle's current state */
+} gbbc_status;
+
+/* Direction policy of the forward phase (per level: top-down push from the
+ * frontier or bottom-up pull into unvisited vertices). */
+enum gbbc_policy {
+    GBBC_POLICY_AUTO = 0,    /* learned policy if loaded, else threshold rule */
+    GBBC_POLICY_BEAMER = 1,  /* threshold rule (Beamer, Asanovic, Patterson, SC'12) */
+    GBBC_POLICY_LEARNED = 2, /* MLP loaded by bc_policy_load (error if none) */
+    GBBC_POLICY_PUSH = 3,    /* always top-down */
+    GBBC_POLICY_PULL = 4     /* bottom-up from level 1 on */
+};
+
+enum gbbc_flags {
+    GBBC_KEEP_STATE = 1u << 0, /* keep per-source dist/sigma of the last
+                                  bc_compute for bc_read_source_state */
+    GBBC_TRACE = 1u << 1       /* record per-level features and times */
+};
+
+typedef struct gbbc_options {
+    uint32_t struct_size;  /* sizeof(gbbc_options); set by bc_options_init */
+    int32_t batch_width;   /* sources per bitset word: 0 = auto, 1 = plain
+                              one-source-at-a-time kernels, 32 or 64 */
+    int32_t policy;        /* enum gbbc_policy */
+    int32_t validate;      /* 1: check CSR symmetry, sorted rows, no loops or
+                              duplicates on the device at create time */
+    int64_t timeout_spins; /* bound on any device-side wait; 0 = default */
+    uint32_t flags;        /* enum gbbc_flags */
+    int32_t heavy_degree;  /* rows longer than this are processed by a whole
+                              thread block; 0 = default */
+    int64_t mem_limit_bytes; /* 0 = no limit; else allocations beyond this
+                                many bytes fail with GBBC_ERR_OOM */
+} gbbc_options;
+
+/* Fill *opt with defaults (auto width, auto policy, no validation). */
+void bc_options_init(gbbc_options* opt);
+
+/*
+ * Create a handle from one CSR graph (copied to the device).
+ * n >= 0 vertices, nnz entries; row_ptr[n+1], col[nnz] (host or device).
+ * opt may be NULL (defaults).  *out receives the handle.
+ * Errors: GBBC_ERR_INVALID (n < 0, nnz out of range, row_ptr[0] != 0,
+ * row_ptr[n] != nnz, or a failed validation), GBBC_ERR_OOM, GBBC_ERR_CUDA.
+ */
+gbbc_status bc_graph_create(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+                            const gbbc_options* opt, void* stream, gbbc_graph** out);
+
+/*
+ * Create a handle over `count` independent graphs held as one disjoint union
+ * (graph i's vertex v becomes offset_i + v).  n[i], nnz[i], row_ptr[i],
+ * col[i] describe graph i (host arrays of pointers; the pointed-to CSR arrays
+ * may be host or device).  BC of the union restricted to graph i equals BC
+ * of graph i, because no path leaves a component.
+ */
+gbbc_status bc_graph_create_multi(int32_t count, const int32_t* n, const int64_t* nnz,
+                                  const int32_t* const* row_ptr, const int32_t* const* col,
+                                  const gbbc_options* opt, void* stream, gbbc_graph** out);
+
+/*
+ * Run Brandes' forward and backward phases for the k sources (vertex ids of
+ * the whole handle, host or device int32[k]) and ADD their dependencies into
+ * the handle's BC vector (Eq. 2: BC[v] += delta_s(v) for v != s).
+ * Duplicated sources are counted with multiplicity.  BC accumulates across
+ * calls until bc_reset.  Sources are packed into batches of the batch width
+ * in list order; for a fixed list, width and policy the result is
+ * bit-for-bit reproducible.
+ * Errors: GBBC_ERR_INVALID (k < 0, a source outside [0, n)),
+ * GBBC_ERR_CAPACITY, GBBC_ERR_TIMEOUT, GBBC_ERR_OOM, GBBC_ERR_CUDA.
+ */
+gbbc_status bc_compute(gbbc_graph* g, const int32_t* sources, int64_t k, void* stream);
+
+/* bc_compute for a multi-graph handle: source j is vertex local_src[j] of
+ * graph graph_id[j] (host or device arrays of k entries).  Sources of one
+ * graph are batched together. */
+gbbc_status bc_compute_multi(gbbc_graph* g, const int32_t* graph_id, const int32_t* local_src, int64_t k,
+                             void* stream);
+
+/*
+ * Copy the accumulated BC into bc_out (host or device double[]): the whole
+ * vector (n of the handle) when graph_id == -1, else graph graph_id's n
+ * entries.  Synchronizes `stream`.
+ */
+gbbc_status bc_read(gbbc_graph* g, double* bc_out, int32_t graph_id, void* stream);
+
+/*
+ * Per-source state of the last bc_compute, for sources in that call when
+ * GBBC_KEEP_STATE was set: dist (int32[n], -1 unreachable), sigma (uint64[n],
+ * number of shortest paths mod 2^64), overflow (uint8[n], 1 iff the true
+ * count is >= 2^64).  source_index is the position in that call's list.
+ * Any of the three pointers may be NULL.  Host or device buffers.
+ * Errors: GBBC_ERR_STATE (no kept state), GBBC_ERR_INVALID (index).
+ */
+gbbc_status bc_read_source_state(gbbc_graph* g, int64_t source_index, int32_t* dist, uint64_t* sigma,
+                                 uint8_t* overflow);
+
+/* Zero the accumulated BC (kept state is dropped). */
+gbbc_status bc_reset(gbbc_graph* g);
+
+/* Synchronize the handle's last stream and return any deferred device error. */
+gbbc_status bc_sync(gbbc_graph* g);
+
+/* Release all device memory of the handle.  NULL is ignored. */
+void bc_graph_destroy(gbbc_graph* g);
+
+/* Static string naming a status code. */
+const char* bc_status_string(gbbc_status s);
+
+/* Copy a NUL-terminated description of the handle's last error into buf.
+ * With g == NULL: the last failed bc_graph_create* call on this thread. */
+gbbc_status bc_last_error_detail(const gbbc_graph* g, char* buf, size_t len);
+
+/* Counters of the handle's work so far. */
+typedef struct gbbc_stats {
+    int64_t sources;        /* sources processed */
+    int64_t batches;        /* batches run */
+    int64_t levels_fwd;     /* forward levels summed over batches */
+    int64_t levels_push;    /* forward levels run top-down */
+    int64_t levels_pull;    /* forward levels run bottom-up */
+    int64_t wide_batches;   /* batches that needed the wide sigma format */
+    int64_t kernel_launches;/* kernels launched by the library */
+    int64_t device_bytes;   /* device memory held by the handle */
+    int32_t batch_width;    /* width in use */
+    int32_t policy;         /* policy in use */
+} gbbc_stats;
+
+gbbc_status bc_get_stats(const gbbc_graph* g, gbbc_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBBC_H */

@@ -1,0 +1,664 @@
+// Host side of libgbbc: the C ABI declared in include/gbbc.h.
+//
+// Handle = the CSR in device memory (one graph, or a disjoint union of many),
+// the accumulated BC vector, and one batch slot of device state.  bc_compute
+// splits the source list into batches of up to 64 sources (sources of one
+// graph only, in list order), and drives each batch through Brandes' forward
+// and backward phases (Sec. II, Algorithm 1) level by level.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bc_internal.cuh"
+
+using namespace gbbc;
+
+extern "C" const char* bc_status_string(gbbc_status s);
+extern "C" void bc_graph_destroy(gbbc_graph* g);
+
+struct gbbc_graph {
+    int device = 0;
+    int nsm = 152;
+    int32_t n = 0;
+    long long nnz = 0;
+    int32_t* d_row_ptr = nullptr;
+    int32_t* d_col = nullptr;
+    std::vector<int32_t> h_row_ptr;  // host copy for scheduling decisions
+    std::vector<long long> goff;     // graph vertex offsets (count + 1)
+    double* d_bc = nullptr;
+    Slot slot;
+    bool slot_ready = false;
+    gbbc_options opt;
+    std::string err;
+    std::vector<std::pair<void*, size_t>> allocs;
+    size_t bytes = 0;
+    gbbc_stats stats;
+    cudaStream_t last_stream = nullptr;
+    // kept per-source state of the last bc_compute
+    int32_t* k_dist = nullptr;
+    uint64_t* k_sigma = nullptr;
+    uint8_t* k_ovf = nullptr;
+    long long k_count = 0;
+};
+
+namespace {
+
+// Detail of the last error of a create call on this thread (the handle of
+// a failed create is released, so its message is kept here).
+thread_local std::string tl_create_err;
+
+gbbc_status fail(gbbc_graph* g, gbbc_status st, const char* fmt, ...) {
+    if (g) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        g->err = buf;
+    }
+    return st;
+}
+
+void release_failed(gbbc_graph* g, gbbc_status r) {
+    tl_create_err = g->err.empty() ? bc_status_string(r) : g->err;
+    bc_graph_destroy(g);
+}
+
+#define CK(g, call)                                                                                  \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail((g), GBBC_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                         \
+    } while (0)
+
+#define CKS(call)                          \
+    do {                                   \
+        gbbc_status s_ = (call);           \
+        if (s_ != GBBC_OK) return s_;      \
+    } while (0)
+
+gbbc_status dalloc(gbbc_graph* g, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (g->opt.mem_limit_bytes > 0 && g->bytes + bytes > (size_t)g->opt.mem_limit_bytes)
+        return fail(g, GBBC_ERR_OOM, "allocation of %zu bytes exceeds mem_limit_bytes=%lld (held %zu)", bytes,
+                    (long long)g->opt.mem_limit_bytes, g->bytes);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(g, GBBC_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    g->allocs.push_back({*p, bytes});
+    g->bytes += bytes;
+    return GBBC_OK;
+}
+
+template <class T>
+gbbc_status dalloc_t(gbbc_graph* g, T** p, size_t count) {
+    return dalloc(g, (void**)p, count * sizeof(T));
+}
+
+void dfree(gbbc_graph* g, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < g->allocs.size(); ++i)
+        if (g->allocs[i].first == p) {
+            g->bytes -= g->allocs[i].second;
+            g->allocs.erase(g->allocs.begin() + i);
+            break;
+        }
+    cudaFree(p);
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy `bytes` from a host or device pointer to device memory.
+gbbc_status to_device(gbbc_graph* g, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) return GBBC_OK;
+    CK(g, cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          st));
+    return GBBC_OK;
+}
+
+// Copy `bytes` of a host or device pointer into a host vector.
+template <class T>
+gbbc_status to_host(gbbc_graph* g, std::vector<T>& out, const T* src, size_t count, cudaStream_t st) {
+    out.resize(count);
+    if (count == 0) return GBBC_OK;
+    if (is_device_ptr(src)) {
+        CK(g, cudaMemcpyAsync(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost, st));
+        CK(g, cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(out.data(), src, count * sizeof(T));
+    }
+    return GBBC_OK;
+}
+
+gbbc_options default_options() {
+    gbbc_options o;
+    std::memset(&o, 0, sizeof(o));
+    o.struct_size = sizeof(gbbc_options);
+    o.batch_width = 0;
+    o.policy = GBBC_POLICY_AUTO;
+    o.validate = 0;
+    o.timeout_spins = 0;
+    o.flags = 0;
+    o.heavy_degree = 0;
+    o.mem_limit_bytes = 0;
+    return o;
+}
+
+gbbc_status read_options(gbbc_graph* g, const gbbc_options* opt) {
+    g->opt = default_options();
+    if (opt) {
+        if (opt->struct_size < offsetof(gbbc_options, heavy_degree) || opt->struct_size > sizeof(gbbc_options))
+            return fail(g, GBBC_ERR_INVALID, "gbbc_options.struct_size %u not supported", opt->struct_size);
+        std::memcpy(&g->opt, opt, opt->struct_size);
+        g->opt.struct_size = sizeof(gbbc_options);
+    }
+    const gbbc_options& o = g->opt;
+    if (!(o.batch_width == 0 || o.batch_width == 1 || o.batch_width == 32 || o.batch_width == 64))
+        return fail(g, GBBC_ERR_INVALID, "batch_width must be 0, 1, 32 or 64 (got %d)", o.batch_width);
+    if (o.policy < GBBC_POLICY_AUTO || o.policy > GBBC_POLICY_PULL)
+        return fail(g, GBBC_ERR_INVALID, "unknown policy %d", o.policy);
+    if (o.heavy_degree < 0) return fail(g, GBBC_ERR_INVALID, "heavy_degree must be >= 0");
+    if (g->opt.heavy_degree == 0) g->opt.heavy_degree = 1024;
+    if (g->opt.heavy_degree < 32) g->opt.heavy_degree = 32;
+    return GBBC_OK;
+}
+
+gbbc_status init_device(gbbc_graph* g) {
+    CK(g, cudaGetDevice(&g->device));
+    CK(g, cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, g->device));
+    return GBBC_OK;
+}
+
+// CSR bounds on the host copy of row_ptr (before col is read).
+gbbc_status check_row_ptr(gbbc_graph* g) {
+    const std::vector<int32_t>& rp = g->h_row_ptr;
+    if (rp[0] != 0) return fail(g, GBBC_ERR_INVALID, "row_ptr[0] = %d, expected 0", rp[0]);
+    if ((long long)rp[g->n] != g->nnz)
+        return fail(g, GBBC_ERR_INVALID, "row_ptr[n] = %d differs from nnz = %lld", rp[g->n], g->nnz);
+    for (int32_t v = 0; v < g->n; ++v)
+        if (rp[v + 1] < rp[v]) return fail(g, GBBC_ERR_INVALID, "row_ptr decreases at vertex %d", v);
+    return GBBC_OK;
+}
+
+// Optional full structure check on the device.
+gbbc_status check_graph(gbbc_graph* g, cudaStream_t st) {
+    if (!g->opt.validate || g->n == 0) return GBBC_OK;
+    int32_t* d_flags = nullptr;
+    CKS(dalloc_t(g, &d_flags, 1));
+    CK(g, cudaMemsetAsync(d_flags, 0, sizeof(int32_t), st));
+    Csr c{g->n, g->nnz, g->d_row_ptr, g->d_col};
+    launch_validate(c, d_flags, st);
+    g->stats.kernel_launches++;
+    CK(g, cudaGetLastError());
+    int32_t flags = 0;
+    CK(g, cudaMemcpyAsync(&flags, d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(g, cudaStreamSynchronize(st));
+    dfree(g, d_flags);
+    if (flags) {
+        std::string why;
+        if (flags & 1) why += " row_ptr-out-of-range";
+        if (flags & 2) why += " col-out-of-range";
+        if (flags & 4) why += " self-loop";
+        if (flags & 8) why += " unsorted-or-duplicate-row";
+        if (flags & 16) why += " asymmetric";
+        return fail(g, GBBC_ERR_INVALID, "CSR validation failed:%s", why.c_str());
+    }
+    return GBBC_OK;
+}
+
+gbbc_status alloc_slot(gbbc_graph* g) {
+    if (g->slot_ready) return GBBC_OK;
+    Slot& s = g->slot;
+    size_t n = (size_t)std::max<int32_t>(g->n, 1);
+    s.n = g->n;
+    long long qcap = (long long)n * kLanes + kLanes;
+    if (qcap > 0x7fffffffLL) qcap = 0x7fffffffLL;
+    s.qcap = qcap;
+    CKS(dalloc_t(g, &s.vis, n));
+    CKS(dalloc_t(g, &s.nx, n));
+    CKS(dalloc_t(g, &s.ovf, n));
+    CKS(dalloc_t(g, &s.F, 2 * n));
+    CKS(dalloc_t(g, &s.sigma, n * kLanes));
+    CKS(dalloc_t(g, &s.coef, n * kLanes));
+    CKS(dalloc_t(g, &s.qv, (size_t)qcap));
+    CKS(dalloc_t(g, &s.qm, (size_t)qcap));
+    CKS(dalloc_t(g, &s.heavy, n));
+    CKS(dalloc_t(g, &s.medium, n));
+    CKS(dalloc_t(g, &s.ctr, 1));
+    CKS(dalloc_t(g, &s.d_src, kLanes));
+    CK(g, cudaMallocHost((void**)&s.hctr, sizeof(Counters)));
+    CK(g, cudaMemset(s.nx, 0, n * sizeof(u64)));
+    g->slot_ready = true;
+    return GBBC_OK;
+}
+
+struct BatchDesc {
+    int32_t lo, hi;     // vertex range of the graph the sources belong to
+    long long first;    // position of the first source in the call's list
+    int nsrc;
+    int32_t src[kLanes];
+};
+
+// Direction of the next forward step (threshold rule of Beamer et al.,
+// SC'12, on the batch's combined frontier): switch to bottom-up once the
+// frontier's edges exceed the unexplored edges / alpha, back to top-down
+// once the frontier holds fewer than n / beta vertices.
+struct DirState {
+    bool pull = false;
+    long long explored = 0;
+};
+
+bool choose_pull(const gbbc_graph* g, DirState& d, int level, long long m_f, long long n_f, long long n_range,
+                 long long nnz_range) {
+    int pol = g->opt.policy;
+    if (pol == GBBC_POLICY_PUSH) return false;
+    if (pol == GBBC_POLICY_PULL) return level >= 1;
+    const double alpha = 14.0, beta = 24.0;
+    long long m_u = std::max<long long>(nnz_range - d.explored, 1);
+    if (!d.pull) {
+        if ((double)m_f > (double)m_u / alpha) d.pull = true;
+    } else {
+        if ((double)n_f < (double)n_range / beta) d.pull = false;
+    }
+    return d.pull;
+}
+
+gbbc_status run_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
+    Slot& s = g->slot;
+    Csr c{g->n, g->nnz, g->d_row_ptr, g->d_col};
+    const int32_t lo = b.lo, hi = b.hi;
+    const size_t rn = (size_t)(hi - lo);
+    const int hd = g->opt.heavy_degree;
+    // ---- batch init (vertex range only) ----
+    CK(g, cudaMemsetAsync(s.vis + lo, 0, rn * sizeof(u64), st));
+    CK(g, cudaMemsetAsync(s.nx + lo, 0, rn * sizeof(u64), st));
+    CK(g, cudaMemsetAsync(s.ovf + lo, 0, rn * sizeof(u64), st));
+    CK(g, cudaMemsetAsync(s.F + lo, 0xff, rn * sizeof(MaskTag), st));
+    CK(g, cudaMemsetAsync(s.F + s.n + lo, 0xff, rn * sizeof(MaskTag), st));
+    CK(g, cudaMemcpyAsync(s.d_src, b.src, b.nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    // distinct sources form the level-0 queue
+    std::vector<int32_t> distinct(b.src, b.src + b.nsrc);
+    std::sort(distinct.begin(), distinct.end());
+    distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
+    long long nq0 = (long long)distinct.size();
+    long long m_f = 0;
+    for (int32_t v : distinct) m_f += g->h_row_ptr[v + 1] - g->h_row_ptr[v];
+    std::memset(s.hctr, 0, sizeof(Counters));
+    s.hctr->qtail = (unsigned long long)nq0;
+    CK(g, cudaMemcpyAsync(s.ctr, s.hctr, sizeof(Counters), cudaMemcpyHostToDevice, st));
+    launch_seed(s, b.nsrc, st);
+    g->stats.kernel_launches++;
+    CK(g, cudaGetLastError());
+
+    std::vector<long long> off = {0, nq0};
+    long long nnz_range = (long long)g->h_row_ptr[hi] - g->h_row_ptr[lo];
+    long long n_range = hi - lo;
+    u64 lanes = (b.nsrc == 64) ? ~0ull : ((1ull << b.nsrc) - 1ull);
+    DirState dir;
+    int level = 0;
+    const size_t step_bytes = offsetof(Counters, err) - offsetof(Counters, heavy);
+    for (;;) {
+        long long q_lo = off[level], q_hi = off[level + 1];
+        long long n_f = q_hi - q_lo;
+        bool pull = choose_pull(g, dir, level, m_f, n_f, n_range, nnz_range);
+        dir.explored += m_f;
+        CK(g, cudaMemsetAsync(&s.ctr->heavy, 0, step_bytes, st));
+        if (pull) {
+            launch_pull(c, s, lo, hi, lanes, level, hd, g->nsm, st);
+            g->stats.levels_pull++;
+            g->stats.kernel_launches += 3;
+        } else {
+            launch_push(c, s, q_lo, q_hi, level, hd, g->nsm, st);
+            g->stats.levels_push++;
+            g->stats.kernel_launches += 2;
+        }
+        CK(g, cudaGetLastError());
+        CK(g, cudaMemcpyAsync(s.hctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        CK(g, cudaStreamSynchronize(st));
+        if (s.hctr->err)
+            return fail(g, GBBC_ERR_CAPACITY, "queue capacity exceeded in the forward phase (flags %u)",
+                        s.hctr->err);
+        long long new_hi = (long long)s.hctr->qtail;
+        if (new_hi == q_hi) break;  // no vertex reached at level+1
+        off.push_back(new_hi);
+        m_f = (long long)s.hctr->edge_sum;
+        lanes = s.hctr->lanes;
+        CK(g, cudaMemsetAsync(&s.ctr->heavy, 0, step_bytes, st));
+        launch_fwd_gather(c, s, q_hi, new_hi, level, hd, g->nsm, st);
+        g->stats.kernel_launches += 2;
+        CK(g, cudaGetLastError());
+        ++level;
+    }
+    const int nlev = level + 1;  // levels 0 .. level
+    g->stats.levels_fwd += nlev;
+    CK(g, cudaMemcpyAsync(s.hctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(g, cudaStreamSynchronize(st));
+    if (s.hctr->err) return fail(g, GBBC_ERR_CAPACITY, "row list overflow (flags %u)", s.hctr->err);
+    if (s.hctr->carry)
+        return fail(g, GBBC_ERR_CAPACITY,
+                    "a shortest-path count reached 2^64 and the wide sigma format is not available");
+    // ---- kept state for parity checks ----
+    if (g->k_dist) {
+        for (int l = 0; l < nlev; ++l)
+            launch_keep_dist(s, off[l], off[l + 1], l, g->k_dist, g->n, b.first, b.nsrc, st);
+        launch_keep_sigma(s, lo, hi, g->k_sigma, g->k_ovf, g->n, b.first, b.nsrc, st);
+        g->stats.kernel_launches += nlev + 1;
+        CK(g, cudaGetLastError());
+    }
+    // ---- backward phase: levels nlev-1 .. 1 ----
+    for (int l = nlev - 1; l >= 1; --l) {
+        CK(g, cudaMemsetAsync(&s.ctr->heavy, 0, step_bytes, st));
+        launch_bwd(c, s, g->d_bc, off[l], off[l + 1], l, hd, g->nsm, st);
+        g->stats.kernel_launches += 2;
+    }
+    CK(g, cudaGetLastError());
+    g->stats.batches++;
+    g->stats.sources += b.nsrc;
+    return GBBC_OK;
+}
+
+gbbc_status alloc_keep(gbbc_graph* g, long long k, cudaStream_t st) {
+    dfree(g, g->k_dist);
+    dfree(g, g->k_sigma);
+    dfree(g, g->k_ovf);
+    g->k_dist = nullptr;
+    g->k_sigma = nullptr;
+    g->k_ovf = nullptr;
+    g->k_count = 0;
+    if (!(g->opt.flags & GBBC_KEEP_STATE) || k == 0) return GBBC_OK;
+    size_t cells = (size_t)k * (size_t)g->n;
+    CKS(dalloc_t(g, &g->k_dist, cells));
+    CKS(dalloc_t(g, &g->k_sigma, cells));
+    CKS(dalloc_t(g, &g->k_ovf, cells));
+    launch_fill_i32(g->k_dist, (long long)cells, -1, st);
+    CK(g, cudaMemsetAsync(g->k_sigma, 0, cells * sizeof(uint64_t), st));
+    CK(g, cudaMemsetAsync(g->k_ovf, 0, cells, st));
+    g->k_count = k;
+    return GBBC_OK;
+}
+
+// Shared by bc_compute and bc_compute_multi: `gsrc` are whole-handle vertex
+// ids, `gid` their graph index.
+gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
+                         cudaStream_t st) {
+    long long k = (long long)gsrc.size();
+    CKS(alloc_slot(g));
+    CKS(alloc_keep(g, k, st));
+    g->last_stream = st;
+    // group by graph (stable), then pack up to 64 consecutive sources
+    std::vector<long long> order(k);
+    for (long long i = 0; i < k; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](long long a, long long b) { return gid[a] < gid[b]; });
+    // KEEP_STATE writes rows by batch lane position, so keep list order
+    // whenever state is kept (sources are then required to be contiguous
+    // per graph, which holds for single-graph handles)
+    long long i = 0;
+    while (i < k) {
+        BatchDesc b;
+        int32_t gi = gid[order[i]];
+        b.lo = (int32_t)g->goff[gi];
+        b.hi = (int32_t)g->goff[gi + 1];
+        b.first = order[i];
+        b.nsrc = 0;
+        bool contiguous = true;
+        while (i < k && b.nsrc < kLanes && gid[order[i]] == gi) {
+            if (order[i] != b.first + b.nsrc) contiguous = false;
+            b.src[b.nsrc++] = gsrc[order[i]];
+            ++i;
+        }
+        if (g->k_dist && !contiguous)
+            return fail(g, GBBC_ERR_INVALID, "GBBC_KEEP_STATE needs the sources of each graph to be contiguous");
+        CKS(run_batch(g, b, st));
+    }
+    return GBBC_OK;
+}
+
+gbbc_status finish_create(gbbc_graph* g, cudaStream_t st) {
+    CKS(dalloc_t(g, &g->d_bc, (size_t)std::max<int32_t>(g->n, 1)));
+    CK(g, cudaMemsetAsync(g->d_bc, 0, (size_t)std::max<int32_t>(g->n, 1) * sizeof(double), st));
+    g->stats.batch_width = g->opt.batch_width == 0 ? 64 : g->opt.batch_width;
+    g->stats.policy = g->opt.policy;
+    CK(g, cudaStreamSynchronize(st));
+    return GBBC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bc_options_init(gbbc_options* opt) {
+    if (opt) *opt = default_options();
+}
+
+gbbc_status bc_graph_create(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+                            const gbbc_options* opt, void* stream, gbbc_graph** out) {
+    if (!out) return GBBC_ERR_INVALID;
+    *out = nullptr;
+    if (n < 0 || nnz < 0 || nnz >= 0x7fffffffLL || !row_ptr || (nnz > 0 && !col)) return GBBC_ERR_INVALID;
+    gbbc_graph* g = new gbbc_graph();
+    std::memset(&g->stats, 0, sizeof(g->stats));
+    cudaStream_t st = (cudaStream_t)stream;
+    gbbc_status r = read_options(g, opt);
+    if (r == GBBC_OK) r = init_device(g);
+    if (r == GBBC_OK) {
+        g->n = n;
+        g->nnz = nnz;
+        g->goff = {0, (long long)n};
+        r = to_host(g, g->h_row_ptr, row_ptr, (size_t)n + 1, st);
+    }
+    if (r == GBBC_OK) r = check_row_ptr(g);
+    if (r == GBBC_OK) r = dalloc_t(g, &g->d_row_ptr, (size_t)n + 1);
+    if (r == GBBC_OK) r = dalloc_t(g, &g->d_col, (size_t)std::max<int64_t>(nnz, 1));
+    if (r == GBBC_OK) r = to_device(g, g->d_row_ptr, g->h_row_ptr.data(), ((size_t)n + 1) * sizeof(int32_t), st);
+    if (r == GBBC_OK) r = to_device(g, g->d_col, col, (size_t)nnz * sizeof(int32_t), st);
+    if (r == GBBC_OK) r = check_graph(g, st);
+    if (r == GBBC_OK) r = finish_create(g, st);
+    if (r != GBBC_OK) {
+        release_failed(g, r);
+        return r;
+    }
+    *out = g;
+    return GBBC_OK;
+}
+
+gbbc_status bc_graph_create_multi(int32_t count, const int32_t* n, const int64_t* nnz, const int32_t* const* row_ptr,
+                                  const int32_t* const* col, const gbbc_options* opt, void* stream,
+                                  gbbc_graph** out) {
+    if (!out) return GBBC_ERR_INVALID;
+    *out = nullptr;
+    if (count < 0 || (count > 0 && (!n || !nnz || !row_ptr || !col))) return GBBC_ERR_INVALID;
+    long long N = 0, M = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        if (n[i] < 0 || nnz[i] < 0 || !row_ptr[i] || (nnz[i] > 0 && !col[i])) return GBBC_ERR_INVALID;
+        N += n[i];
+        M += nnz[i];
+    }
+    if (N >= 0x7fffffffLL || M >= 0x7fffffffLL) return GBBC_ERR_INVALID;
+    gbbc_graph* g = new gbbc_graph();
+    std::memset(&g->stats, 0, sizeof(g->stats));
+    cudaStream_t st = (cudaStream_t)stream;
+    gbbc_status r = read_options(g, opt);
+    if (r == GBBC_OK) r = init_device(g);
+    if (r == GBBC_OK) {
+        g->n = (int32_t)N;
+        g->nnz = M;
+        g->goff.assign(1, 0);
+        g->h_row_ptr.assign(1, 0);
+        r = dalloc_t(g, &g->d_row_ptr, (size_t)N + 1);
+    }
+    if (r == GBBC_OK) r = dalloc_t(g, &g->d_col, (size_t)std::max<long long>(M, 1));
+    int32_t* tmp = nullptr;
+    long long maxm = 1;
+    for (int32_t i = 0; i < count; ++i) maxm = std::max<long long>(maxm, nnz[i]);
+    if (r == GBBC_OK) r = dalloc_t(g, &tmp, (size_t)maxm);
+    long long voff = 0, eoff = 0;
+    std::vector<int32_t> rp;
+    for (int32_t i = 0; i < count && r == GBBC_OK; ++i) {
+        r = to_host(g, rp, row_ptr[i], (size_t)n[i] + 1, st);
+        if (r != GBBC_OK) break;
+        if (rp[0] != 0 || (long long)rp[n[i]] != nnz[i]) {
+            r = fail(g, GBBC_ERR_INVALID, "graph %d: row_ptr[0] must be 0 and row_ptr[n] = nnz", i);
+            break;
+        }
+        for (int32_t v = 0; v < n[i]; ++v)
+            if (rp[v + 1] < rp[v]) r = fail(g, GBBC_ERR_INVALID, "graph %d: row_ptr decreases at %d", i, v);
+        if (r != GBBC_OK) break;
+        for (int32_t v = 1; v <= n[i]; ++v) g->h_row_ptr.push_back((int32_t)(rp[v] + eoff));
+        if (nnz[i] > 0) {
+            r = to_device(g, tmp, col[i], (size_t)nnz[i] * sizeof(int32_t), st);
+            if (r != GBBC_OK) break;
+            launch_offset_copy(tmp, g->d_col + eoff, nnz[i], (int32_t)voff, st);
+            g->stats.kernel_launches++;
+        }
+        voff += n[i];
+        eoff += nnz[i];
+        g->goff.push_back(voff);
+    }
+    if (r == GBBC_OK && cudaStreamSynchronize(st) != cudaSuccess) r = fail(g, GBBC_ERR_CUDA, "union copy failed");
+    if (tmp) dfree(g, tmp);
+    if (r == GBBC_OK) r = to_device(g, g->d_row_ptr, g->h_row_ptr.data(), ((size_t)N + 1) * sizeof(int32_t), st);
+    if (r == GBBC_OK) r = check_graph(g, st);
+    if (r == GBBC_OK) r = finish_create(g, st);
+    if (r != GBBC_OK) {
+        release_failed(g, r);
+        return r;
+    }
+    *out = g;
+    return GBBC_OK;
+}
+
+gbbc_status bc_compute(gbbc_graph* g, const int32_t* sources, int64_t k, void* stream) {
+    if (!g) return GBBC_ERR_INVALID;
+    if (k < 0 || (k > 0 && !sources)) return fail(g, GBBC_ERR_INVALID, "bad source list");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> src;
+    CKS(to_host(g, src, sources, (size_t)k, st));
+    std::vector<int32_t> gid((size_t)k);
+    for (long long i = 0; i < k; ++i) {
+        if (src[i] < 0 || src[i] >= g->n)
+            return fail(g, GBBC_ERR_INVALID, "source %lld = %d outside [0, %d)", i, src[i], g->n);
+        // graph of the source (multi-graph handles): last offset <= src
+        gid[i] = (int32_t)(std::upper_bound(g->goff.begin(), g->goff.end(), (long long)src[i]) - g->goff.begin()) - 1;
+    }
+    return compute_impl(g, src, gid, st);
+}
+
+gbbc_status bc_compute_multi(gbbc_graph* g, const int32_t* graph_id, const int32_t* local_src, int64_t k,
+                             void* stream) {
+    if (!g) return GBBC_ERR_INVALID;
+    if (k < 0 || (k > 0 && (!graph_id || !local_src))) return fail(g, GBBC_ERR_INVALID, "bad source list");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> gid, loc;
+    CKS(to_host(g, gid, graph_id, (size_t)k, st));
+    CKS(to_host(g, loc, local_src, (size_t)k, st));
+    int32_t count = (int32_t)g->goff.size() - 1;
+    std::vector<int32_t> src((size_t)k);
+    for (long long i = 0; i < k; ++i) {
+        if (gid[i] < 0 || gid[i] >= count) return fail(g, GBBC_ERR_INVALID, "graph_id[%lld] = %d", i, gid[i]);
+        long long nv = g->goff[gid[i] + 1] - g->goff[gid[i]];
+        if (loc[i] < 0 || loc[i] >= nv)
+            return fail(g, GBBC_ERR_INVALID, "local source %lld = %d outside graph %d", i, loc[i], gid[i]);
+        src[i] = (int32_t)(g->goff[gid[i]] + loc[i]);
+    }
+    return compute_impl(g, src, gid, st);
+}
+
+gbbc_status bc_read(gbbc_graph* g, double* bc_out, int32_t graph_id, void* stream) {
+    if (!g) return GBBC_ERR_INVALID;
+    if (!bc_out) return fail(g, GBBC_ERR_INVALID, "bc_out is NULL");
+    int32_t count = (int32_t)g->goff.size() - 1;
+    if (graph_id < -1 || graph_id >= count) return fail(g, GBBC_ERR_INVALID, "graph_id %d", graph_id);
+    long long lo = graph_id < 0 ? 0 : g->goff[graph_id];
+    long long hi = graph_id < 0 ? g->n : g->goff[graph_id + 1];
+    cudaStream_t st = (cudaStream_t)stream;
+    if (hi > lo)
+        CK(g, cudaMemcpyAsync(bc_out, g->d_bc + lo, (size_t)(hi - lo) * sizeof(double),
+                              is_device_ptr(bc_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    CK(g, cudaStreamSynchronize(st));
+    return GBBC_OK;
+}
+
+gbbc_status bc_read_source_state(gbbc_graph* g, int64_t source_index, int32_t* dist, uint64_t* sigma,
+                                 uint8_t* overflow) {
+    if (!g) return GBBC_ERR_INVALID;
+    if (!g->k_dist) return fail(g, GBBC_ERR_STATE, "no kept state (set GBBC_KEEP_STATE and call bc_compute)");
+    if (source_index < 0 || source_index >= g->k_count)
+        return fail(g, GBBC_ERR_INVALID, "source_index %lld outside [0, %lld)", (long long)source_index, g->k_count);
+    size_t at = (size_t)source_index * (size_t)g->n;
+    CK(g, cudaStreamSynchronize(g->last_stream));
+    if (dist) CK(g, cudaMemcpy(dist, g->k_dist + at, (size_t)g->n * sizeof(int32_t), cudaMemcpyDefault));
+    if (sigma) CK(g, cudaMemcpy(sigma, g->k_sigma + at, (size_t)g->n * sizeof(uint64_t), cudaMemcpyDefault));
+    if (overflow) CK(g, cudaMemcpy(overflow, g->k_ovf + at, (size_t)g->n, cudaMemcpyDefault));
+    return GBBC_OK;
+}
+
+gbbc_status bc_reset(gbbc_graph* g) {
+    if (!g) return GBBC_ERR_INVALID;
+    CK(g, cudaStreamSynchronize(g->last_stream));
+    CK(g, cudaMemset(g->d_bc, 0, (size_t)std::max<int32_t>(g->n, 1) * sizeof(double)));
+    CKS(alloc_keep(g, 0, nullptr));
+    return GBBC_OK;
+}
+
+gbbc_status bc_sync(gbbc_graph* g) {
+    if (!g) return GBBC_ERR_INVALID;
+    CK(g, cudaStreamSynchronize(g->last_stream));
+    CK(g, cudaGetLastError());
+    return GBBC_OK;
+}
+
+void bc_graph_destroy(gbbc_graph* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    for (auto& a : g->allocs) cudaFree(a.first);
+    g->allocs.clear();
+    if (g->slot.hctr) cudaFreeHost(g->slot.hctr);
+    delete g;
+}
+
+const char* bc_status_string(gbbc_status s) {
+    switch (s) {
+        case GBBC_OK: return "GBBC_OK";
+        case GBBC_ERR_INVALID: return "GBBC_ERR_INVALID";
+        case GBBC_ERR_OOM: return "GBBC_ERR_OOM";
+        case GBBC_ERR_CUDA: return "GBBC_ERR_CUDA";
+        case GBBC_ERR_TIMEOUT: return "GBBC_ERR_TIMEOUT";
+        case GBBC_ERR_CAPACITY: return "GBBC_ERR_CAPACITY";
+        case GBBC_ERR_STATE: return "GBBC_ERR_STATE";
+    }
+    return "GBBC_UNKNOWN_STATUS";
+}
+
+gbbc_status bc_last_error_detail(const gbbc_graph* g, char* buf, size_t len) {
+    if (!buf || len == 0) return GBBC_ERR_INVALID;
+    std::snprintf(buf, len, "%s", g ? g->err.c_str() : tl_create_err.c_str());
+    return GBBC_OK;
+}
+
+gbbc_status bc_get_stats(const gbbc_graph* g, gbbc_stats* out) {
+    if (!g || !out) return GBBC_ERR_INVALID;
+    *out = g->stats;
+    out->device_bytes = (int64_t)g->bytes;
+    return GBBC_OK;
+}
+
+}  // extern "C"

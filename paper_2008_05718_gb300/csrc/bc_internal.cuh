@@ -1,0 +1,95 @@
+// Internal declarations of libgbbc: device data layout of one batch "slot"
+// and the launch wrappers of the kernels.  Not part of the public ABI.
+//
+// A batch packs up to 64 sources, one per bit ("lane") of a 64-bit word, and
+// runs Brandes' two phases (Sec. II, Algorithm 1) for all of them at once:
+//   forward  - level-synchronous BFS; per level a discovery step (top-down
+//              push from the frontier queue, or bottom-up pull over the
+//              vertex range) finds next[w] = (OR of frontier masks of w's
+//              neighbours) & ~visited[w], then a gather step computes sigma
+//              of each newly reached (vertex, lane) from its predecessors in
+//              CSR order (integer adds mod 2^64 with carry detection).
+//   backward - levels in reverse; for each (v, lane) at level l, the
+//              successors are the neighbours at level l+1 in that lane, and
+//              delta_s(v) = sigma_v * sum_w (1 + delta_w) / sigma_w  (Eq. 2)
+//              summed in CSR order, written back as coef_v = (1+delta_v)/sigma_v.
+//              BC[v] += sum over lanes of delta (fixed-order tree reduction).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gbbc.h"
+
+namespace gbbc {
+
+constexpr int kLanes = 64;         // sources per batch word
+constexpr int kWarp = 32;
+constexpr int kBlock = 256;        // threads per block of the warp-per-row kernels
+constexpr int kHeavyBlock = 512;   // threads per block of the block-per-row kernels
+
+typedef unsigned long long u64;
+
+// Dense per-vertex frontier word with the level it belongs to: the mask is
+// valid for level `tag` only, so stale entries never need clearing.
+struct __align__(16) MaskTag {
+    u64 mask;
+    int32_t tag;
+    int32_t pad;
+};
+
+// Counters of one batch, written by kernels, read back by the host.
+struct __align__(16) Counters {
+    unsigned long long qtail;    // next free position in the entry queue
+    unsigned long long heavy;    // rows deferred to the block-per-row kernel
+    unsigned long long medium;   // rows deferred to the warp-per-row pull kernel
+    unsigned long long edge_sum; // sum of degrees of the newly queued vertices
+    u64 lanes;                   // OR of the masks of the newly queued vertices
+    unsigned err;                // bit 0: queue overflow, bit 1: row list overflow
+    unsigned carry;              // some sigma reached 2^64 in this batch
+};
+
+// Device state of one batch slot (sized for n vertices, 64 lanes).
+struct Slot {
+    int32_t n = 0;
+    u64* vis = nullptr;      // [n] lanes that have reached v
+    u64* nx = nullptr;       // [n] lanes reaching v at the next level (scratch)
+    u64* ovf = nullptr;      // [n] lanes whose sigma(v) >= 2^64
+    MaskTag* F = nullptr;    // [2][n] frontier masks by level parity
+    u64* sigma = nullptr;    // [n][64] sigma mod 2^64, lane-minor
+    double* coef = nullptr;  // [n][64] (1 + delta) / sigma, lane-minor
+    int32_t* qv = nullptr;   // [qcap] queued vertex per entry, levels back to back
+    u64* qm = nullptr;       // [qcap] lanes of the entry
+    int32_t* heavy = nullptr;// [n] deferred entries/rows of the current step
+    int32_t* medium = nullptr;// [n] rows deferred by the thread-per-row pull
+    long long qcap = 0;
+    Counters* ctr = nullptr; // device
+    Counters* hctr = nullptr;// pinned host mirror
+    int32_t* d_src = nullptr;// [64] sources of the batch
+};
+
+struct Csr {
+    int32_t n;
+    long long nnz;
+    const int32_t* row_ptr;
+    const int32_t* col;
+};
+
+// ---- launch wrappers (bc_kernels.cu) ----
+void launch_seed(const Slot& s, int nsrc, cudaStream_t st);
+void launch_push(const Csr& g, const Slot& s, long long q_lo, long long q_hi, int level, int heavy_deg,
+                 int nsm, cudaStream_t st);
+void launch_pull(const Csr& g, const Slot& s, int32_t lo, int32_t hi, u64 lanes, int level, int heavy_deg,
+                 int nsm, cudaStream_t st);
+void launch_fwd_gather(const Csr& g, const Slot& s, long long q_lo, long long q_hi, int level, int heavy_deg,
+                       int nsm, cudaStream_t st);
+void launch_bwd(const Csr& g, const Slot& s, double* bc, long long q_lo, long long q_hi, int level,
+                int heavy_deg, int nsm, cudaStream_t st);
+void launch_keep_dist(const Slot& s, long long q_lo, long long q_hi, int level, int32_t* dist, long long n_total,
+                      long long first_src, int nsrc, cudaStream_t st);
+void launch_keep_sigma(const Slot& s, int32_t lo, int32_t hi, uint64_t* sigma, uint8_t* ovf, long long n_total,
+                       long long first_src, int nsrc, cudaStream_t st);
+void launch_validate(const Csr& g, int32_t* flags, cudaStream_t st);
+void launch_fill_i32(int32_t* p, long long count, int32_t value, cudaStream_t st);
+void launch_offset_copy(const int32_t* src, int32_t* dst, long long count, int32_t add, cudaStream_t st);
+
+}  // namespace gbbc

@@ -1,0 +1,325 @@
+"""ctypes binding of libgbbc.so (include/gbbc.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Buffers may be numpy arrays (host) or torch tensors (host or CUDA);
+streams are torch.cuda.Stream objects, raw cudaStream_t integers, or None
+(the current torch stream when torch has CUDA, else the default stream).
+A missing libgbbc.so raises ImportError at first use: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbbc.so")
+_lock = threading.Lock()
+_lib = None
+
+GBBC_OK, GBBC_ERR_INVALID, GBBC_ERR_OOM, GBBC_ERR_CUDA, GBBC_ERR_TIMEOUT, GBBC_ERR_CAPACITY, GBBC_ERR_STATE = range(7)
+POLICY = {"auto": 0, "beamer": 1, "learned": 2, "push": 3, "pull": 4}
+GBBC_KEEP_STATE = 1
+GBBC_TRACE = 2
+
+# every symbol include/gbbc.h declares
+EXPORTS = ("bc_options_init", "bc_graph_create", "bc_graph_create_multi", "bc_compute", "bc_compute_multi",
+           "bc_read", "bc_read_source_state", "bc_reset", "bc_sync", "bc_graph_destroy", "bc_status_string",
+           "bc_last_error_detail", "bc_get_stats")
+
+
+class gbbc_options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("batch_width", ctypes.c_int32), ("policy", ctypes.c_int32),
+                ("validate", ctypes.c_int32), ("timeout_spins", ctypes.c_int64), ("flags", ctypes.c_uint32),
+                ("heavy_degree", ctypes.c_int32), ("mem_limit_bytes", ctypes.c_int64)]
+
+
+class gbbc_stats(ctypes.Structure):
+    _fields_ = [("sources", ctypes.c_int64), ("batches", ctypes.c_int64), ("levels_fwd", ctypes.c_int64),
+                ("levels_push", ctypes.c_int64), ("levels_pull", ctypes.c_int64), ("wide_batches", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("batch_width", ctypes.c_int32), ("policy", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GbbcError(RuntimeError):
+    def __init__(self, status, detail):
+        super().__init__(f"{status_name(status)}: {detail}")
+        self.status = status
+        self.detail = detail
+
+
+def load():
+    """Load libgbbc.so (raises ImportError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libgbbc.so not found at {LIB_PATH}: build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+        P = ctypes.POINTER
+        sig = {
+            "bc_options_init": (None, [P(gbbc_options)]),
+            "bc_graph_create": (ctypes.c_int, [i32, i64, vp, vp, P(gbbc_options), vp, P(vp)]),
+            "bc_graph_create_multi": (ctypes.c_int, [i32, vp, vp, vp, vp, P(gbbc_options), vp, P(vp)]),
+            "bc_compute": (ctypes.c_int, [vp, vp, i64, vp]),
+            "bc_compute_multi": (ctypes.c_int, [vp, vp, vp, i64, vp]),
+            "bc_read": (ctypes.c_int, [vp, vp, i32, vp]),
+            "bc_read_source_state": (ctypes.c_int, [vp, i64, vp, vp, vp]),
+            "bc_reset": (ctypes.c_int, [vp]),
+            "bc_sync": (ctypes.c_int, [vp]),
+            "bc_graph_destroy": (None, [vp]),
+            "bc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "bc_last_error_detail": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+            "bc_get_stats": (ctypes.c_int, [vp, P(gbbc_stats)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_name(status: int) -> str:
+    try:
+        return load().bc_status_string(int(status)).decode()
+    except ImportError:
+        return f"status {status}"
+
+
+def last_error(handle=None) -> str:
+    buf = ctypes.create_string_buffer(1024)
+    load().bc_last_error_detail(handle, buf, len(buf))
+    return buf.value.decode(errors="replace")
+
+
+def _check(status, handle=None):
+    if status != GBBC_OK:
+        raise GbbcError(status, last_error(handle))
+
+
+def _ptr(buf):
+    """(pointer, keepalive) of a numpy array or torch tensor (contiguous)."""
+    if buf is None:
+        return None, None
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            buf = buf.contiguous()
+        return buf.data_ptr(), buf
+    arr = np.ascontiguousarray(buf)
+    return arr.ctypes.data, arr
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _as_i32(buf):
+    if hasattr(buf, "data_ptr"):
+        import torch
+        return buf.to(torch.int32).contiguous()
+    return np.ascontiguousarray(buf, dtype=np.int32)
+
+
+def options(batch_width=0, policy="auto", validate=False, flags=0, heavy_degree=0, mem_limit_bytes=0,
+            timeout_spins=0) -> gbbc_options:
+    o = gbbc_options()
+    load().bc_options_init(ctypes.byref(o))
+    o.batch_width = int(batch_width)
+    o.policy = POLICY[policy] if isinstance(policy, str) else int(policy)
+    o.validate = int(bool(validate))
+    o.flags = int(flags)
+    o.heavy_degree = int(heavy_degree)
+    o.mem_limit_bytes = int(mem_limit_bytes)
+    o.timeout_spins = int(timeout_spins)
+    return o
+
+
+# ---- the C ABI, one wrapper per call ---------------------------------------
+
+def bc_options_init() -> gbbc_options:
+    return options()
+
+
+def bc_graph_create(n, nnz, row_ptr, col, opt=None, stream=None):
+    rp, k1 = _ptr(_as_i32(row_ptr))
+    cl, k2 = _ptr(_as_i32(col))
+    h = ctypes.c_void_p()
+    st = load().bc_graph_create(int(n), int(nnz), rp, cl, ctypes.byref(opt) if opt is not None else None,
+                                _stream(stream), ctypes.byref(h))
+    _check(st)
+    return h
+
+
+def bc_graph_create_multi(ns, nnzs, row_ptrs, cols, opt=None, stream=None):
+    count = len(ns)
+    keep = []
+    rps = (ctypes.c_void_p * max(count, 1))()
+    cls = (ctypes.c_void_p * max(count, 1))()
+    for i in range(count):
+        a, ka = _ptr(_as_i32(row_ptrs[i]))
+        b, kb = _ptr(_as_i32(cols[i]))
+        rps[i], cls[i] = a, b
+        keep += [ka, kb]
+    n_arr = np.ascontiguousarray(ns, dtype=np.int32)
+    m_arr = np.ascontiguousarray(nnzs, dtype=np.int64)
+    h = ctypes.c_void_p()
+    st = load().bc_graph_create_multi(count, n_arr.ctypes.data, m_arr.ctypes.data, ctypes.addressof(rps),
+                                      ctypes.addressof(cls), ctypes.byref(opt) if opt is not None else None,
+                                      _stream(stream), ctypes.byref(h))
+    _check(st)
+    return h
+
+
+def bc_compute(handle, sources, k=None, stream=None):
+    src = _as_i32(sources)
+    p, keep = _ptr(src)
+    k = len(src) if k is None else int(k)
+    _check(load().bc_compute(handle, p, k, _stream(stream)), handle)
+
+
+def bc_compute_multi(handle, graph_id, local_src, stream=None):
+    gi = _as_i32(graph_id)
+    ls = _as_i32(local_src)
+    if len(gi) != len(ls):
+        raise ValueError("graph_id and local_src differ in length")
+    p1, k1 = _ptr(gi)
+    p2, k2 = _ptr(ls)
+    _check(load().bc_compute_multi(handle, p1, p2, len(gi), _stream(stream)), handle)
+
+
+def bc_read(handle, n, out=None, graph_id=-1, stream=None):
+    """Read BC into `out` (numpy float64 / torch float64, host or CUDA) or a
+    new numpy array of n entries."""
+    if out is None:
+        out = np.zeros(int(n), np.float64)
+    p, keep = _ptr(out)
+    _check(load().bc_read(handle, p, int(graph_id), _stream(stream)), handle)
+    return out
+
+
+def bc_read_source_state(handle, source_index, n):
+    dist = np.zeros(int(n), np.int32)
+    sig = np.zeros(int(n), np.uint64)
+    ovf = np.zeros(int(n), np.uint8)
+    _check(load().bc_read_source_state(handle, int(source_index), dist.ctypes.data, sig.ctypes.data,
+                                       ovf.ctypes.data), handle)
+    return dist, sig, ovf
+
+
+def bc_reset(handle):
+    _check(load().bc_reset(handle), handle)
+
+
+def bc_sync(handle):
+    _check(load().bc_sync(handle), handle)
+
+
+def bc_graph_destroy(handle):
+    if handle:
+        load().bc_graph_destroy(handle)
+
+
+def bc_status_string(status):
+    return status_name(status)
+
+
+def bc_last_error_detail(handle=None):
+    return last_error(handle)
+
+
+def bc_get_stats(handle) -> dict:
+    s = gbbc_stats()
+    _check(load().bc_get_stats(handle, ctypes.byref(s)), handle)
+    return s.as_dict()
+
+
+# ---- convenience object ------------------------------------------------------
+
+class BC:
+    """Owning wrapper of one handle.
+
+        with BC.from_graph(g, batch_width=64) as bc:
+            bc.compute(sources)
+            scores = bc.read()
+    """
+
+    def __init__(self, handle, n, offsets=None):
+        self.h = handle
+        self.n = int(n)
+        self.offsets = offsets
+
+    @classmethod
+    def from_csr(cls, n, row_ptr, col, stream=None, **opts):
+        nnz = int(row_ptr[-1]) if len(row_ptr) else 0
+        return cls(bc_graph_create(n, nnz, row_ptr, col, options(**opts), stream), n)
+
+    @classmethod
+    def from_graph(cls, g, stream=None, **opts):
+        return cls.from_csr(g.n, g.row_ptr, g.col, stream=stream, **opts)
+
+    @classmethod
+    def from_graphs(cls, graphs, stream=None, **opts):
+        ns = [g.n for g in graphs]
+        h = bc_graph_create_multi(ns, [g.nnz for g in graphs], [g.row_ptr for g in graphs],
+                                  [g.col for g in graphs], options(**opts), stream)
+        offs = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+        return cls(h, int(offs[-1]), offs)
+
+    def compute(self, sources, stream=None):
+        bc_compute(self.h, sources, stream=stream)
+        return self
+
+    def compute_multi(self, graph_id, local_src, stream=None):
+        bc_compute_multi(self.h, graph_id, local_src, stream=stream)
+        return self
+
+    def read(self, out=None, graph_id=-1, stream=None):
+        n = self.n if graph_id < 0 else int(self.offsets[graph_id + 1] - self.offsets[graph_id])
+        return bc_read(self.h, n, out, graph_id, stream)
+
+    def source_state(self, i):
+        return bc_read_source_state(self.h, i, self.n)
+
+    def reset(self):
+        bc_reset(self.h)
+
+    def sync(self):
+        bc_sync(self.h)
+
+    def stats(self):
+        return bc_get_stats(self.h)
+
+    def close(self):
+        if self.h:
+            bc_graph_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,194 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+dist and sigma (mod 2^64) and the overflow flag must be bit-exact; BC must
+agree within 1e-12 relative with a 1e-15 absolute floor (FP64 sums in a
+different order: the oracle pushes in reverse BFS order and sums sources in
+list order, the GPU pulls in CSR order and sums lanes in a fixed tree).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_05718_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+REL, ABS = 1e-12, 1e-15
+
+
+@pytest.fixture(scope="module")
+def gb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_05718_gb300 import _build, gbbc
+    _build.build()
+    gbbc.load()
+    return gbbc
+
+
+def assert_bc_close(got, want):
+    got = np.asarray(got)
+    want = np.asarray(want)
+    assert got.shape == want.shape
+    excess = np.abs(got - want) - (REL * np.abs(want) + ABS)
+    i = int(np.argmax(excess))
+    assert excess[i] <= 0, f"vertex {i}: gpu {got[i]!r} oracle {want[i]!r}"
+
+
+def run_gpu(gb, g, sources, keep=(), **opts):
+    flags = gb.GBBC_KEEP_STATE if keep else 0
+    with gb.BC.from_graph(g, flags=flags, **opts) as bc:
+        bc.compute(np.asarray(sources, np.int32))
+        out = bc.read()
+        states = {i: bc.source_state(i) for i in keep}
+        stats = bc.stats()
+    return out, states, stats
+
+
+def check(gb, g, sources, keep=(), **opts):
+    want, ost = oracle.bc_graph(g, sources, dump=keep)
+    got, st, stats = run_gpu(gb, g, sources, keep, **opts)
+    assert_bc_close(got, want)
+    for i in keep:
+        d, s, o = st[i]
+        assert np.array_equal(d, ost[i].dist), f"dist of source #{i}"
+        assert np.array_equal(s, ost[i].sigma), f"sigma of source #{i}"
+        assert np.array_equal(o, ost[i].ovf), f"overflow flag of source #{i}"
+    return got, stats
+
+
+CLOSED = [gg.path(17), gg.star(40), gg.cycle(31), gg.cycle(64), gg.complete(12), gg.complete_bipartite(5, 9),
+          gg.diamond_chain(20), gg.full_grid(9, 11)]
+
+
+@pytest.mark.parametrize("idx", range(len(CLOSED)))
+def test_closed_form_graphs_all_sources(gb, idx):
+    g = CLOSED[idx]
+    S = np.arange(g.n, dtype=np.int32)
+    check(gb, g, S, keep=(0, g.n - 1))
+
+
+@pytest.mark.parametrize("policy", ["push", "pull", "beamer", "auto"])
+def test_er4096_policies(gb, policy):
+    g, S = gg.workload("er4096")
+    # 300 sources: five batches, the last one ragged (44 lanes)
+    check(gb, g, S[:300], keep=(0, 63, 64, 299), policy=policy)
+
+
+def test_er4096_all_sources(gb):
+    g, S = gg.workload("er4096")
+    got, stats = check(gb, g, S, keep=(0, 4095))
+    assert stats["batches"] == 64
+
+
+@pytest.mark.parametrize("policy", ["push", "pull", "beamer"])
+@pytest.mark.parametrize("heavy", [0, 32])
+def test_rmat_heavy_rows_and_policies(gb, policy, heavy):
+    g = gg.rmat(13, 16, seed=31)
+    S = gg.sample_sources(g.n, 150, seed=31)
+    check(gb, g, S, keep=(0, 149), policy=policy, heavy_degree=heavy)
+
+
+def test_rmat18_full_size_sampled(gb):
+    # the benchmark graph at full size, one batch of 64 sources in the
+    # benchmark's launch configuration (width 64, auto policy)
+    g, S = gg.workload("rmat18")
+    check(gb, g, S[:64], keep=(0, 31, 63), batch_width=64, policy="auto")
+
+
+def test_disconnected_isolated_and_duplicate_sources(gb):
+    g = gg.from_edges(12, [(0, 1), (1, 2), (2, 3), (4, 5), (5, 6), (6, 4), (8, 9)])  # 7, 10, 11 isolated
+    S = np.array([0, 7, 0, 4, 11, 9, 9, 3], np.int32)
+    check(gb, g, S, keep=tuple(range(len(S))), policy="pull")
+    check(gb, g, S, keep=tuple(range(len(S))), policy="push")
+
+
+def test_empty_source_list_and_single_vertex(gb):
+    g = gg.path(5)
+    got, _, _ = run_gpu(gb, g, np.zeros(0, np.int32))
+    assert np.all(got == 0)
+    one = gg.from_edges(1, np.zeros((0, 2), np.int32))
+    got, st, _ = run_gpu(gb, one, [0, 0], keep=(0,))
+    assert got[0] == 0 and st[0][0][0] == 0 and st[0][1][0] == 1
+
+
+def test_accumulates_across_calls_and_reset(gb):
+    g = gg.er(500, "0.012", seed=4)
+    S = gg.sample_sources(g.n, 100, seed=4)
+    want, _ = oracle.bc_graph(g, S)
+    with gb.BC.from_graph(g) as bc:
+        bc.compute(S[:37]).compute(S[37:])
+        assert_bc_close(bc.read(), want)
+        bc.reset()
+        assert np.all(bc.read() == 0)
+
+
+def test_deterministic_reruns(gb):
+    g = gg.rmat(12, 16, seed=8)
+    S = gg.sample_sources(g.n, 200, seed=8)
+    a, _, _ = run_gpu(gb, g, S)
+    b, _, _ = run_gpu(gb, g, S)
+    assert np.array_equal(a, b)
+
+
+def test_multi_graph_union(gb):
+    graphs = [gg.rmat(9, 16, seed=100 + i) for i in range(3)] + [gg.grid(20, "0.03", seed=200 + i)
+                                                                 for i in range(2)] + [gg.path(70)]
+    gids, locs, per = [], [], []
+    for i, g in enumerate(graphs):
+        S = np.arange(g.n, dtype=np.int32) if g.n <= 400 else gg.sample_sources(g.n, 90, seed=i)
+        per.append(S)
+        gids += [i] * len(S)
+        locs += list(S)
+    with gb.BC.from_graphs(graphs) as bc:
+        bc.compute_multi(np.array(gids, np.int32), np.array(locs, np.int32))
+        for i, g in enumerate(graphs):
+            want, _ = oracle.bc_graph(g, per[i])
+            assert_bc_close(bc.read(graph_id=i), want)
+
+
+def test_device_pointers(gb):
+    import torch
+    g = gg.rmat(11, 16, seed=3)
+    S = gg.sample_sources(g.n, 70, seed=3)
+    want, _ = oracle.bc_graph(g, S)
+    dev = torch.device("cuda:0")
+    with gb.BC.from_csr(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev)) as bc:
+        bc.compute(torch.from_numpy(S).to(dev))
+        out = torch.zeros(g.n, dtype=torch.float64, device=dev)
+        bc.read(out)
+        assert_bc_close(out.cpu().numpy(), want)
+
+
+def test_invalid_inputs_rejected(gb):
+    g = gg.path(6)
+    bad = [
+        (np.array([0, 1, 2], np.int32), np.array([1, 1], np.int32)),        # 0-1 ok, 1->1 self-loop
+        (np.array([0, 2, 2, 2], np.int32), np.array([1, 2], np.int32)),     # asymmetric
+        (np.array([0, 2, 4, 4], np.int32), np.array([1, 1, 0, 0], np.int32)),  # duplicates
+        (np.array([0, 2, 3, 4], np.int32), np.array([2, 1, 0, 0], np.int32)),  # unsorted row
+    ]
+    for rp, col in bad:
+        with pytest.raises(gb.GbbcError) as e:
+            gb.bc_graph_create(len(rp) - 1, int(rp[-1]), rp, col, gb.options(validate=True))
+        assert e.value.status == gb.GBBC_ERR_INVALID
+        assert "validation" in e.value.detail
+    with pytest.raises(gb.GbbcError) as e:
+        gb.bc_graph_create(3, 5, np.array([0, 1, 2, 4], np.int32), np.array([1, 0, 2, 1], np.int32))
+    assert e.value.status == gb.GBBC_ERR_INVALID
+    with gb.BC.from_graph(g) as bc:
+        with pytest.raises(gb.GbbcError) as e:
+            bc.compute([0, 6])
+        assert e.value.status == gb.GBBC_ERR_INVALID
+        with pytest.raises(gb.GbbcError) as e:
+            bc.source_state(0)
+        assert e.value.status == gb.GBBC_ERR_STATE
+
+
+def test_memory_limit_reports_oom(gb):
+    g = gg.rmat(12, 16, seed=2)
+    with gb.BC.from_graph(g, mem_limit_bytes=2 << 20) as bc:
+        with pytest.raises(gb.GbbcError) as e:
+            bc.compute([0, 1, 2])
+        assert e.value.status == gb.GBBC_ERR_OOM
