@@ -1,0 +1,320 @@
+"""Benchmark: exact Brandes BC throughput in GTEPS (sources x directed edges / s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat18]
+                    [--policy auto] [--width 64] [--impl ours|reference]
+
+One step = one bc_compute over the workload's whole source list (forward,
+backward and BC accumulation for every source) followed by bc_read of the
+BC vector into device memory; the graph and sources are resident in HBM.
+An L2 flush (a 512 MiB device write) separates timed steps and is not timed.
+Steps are timed with CUDA events on the compute stream.  `e2e` times the same
+metric through the C ABI with host buffers: bc_graph_create from pinned host
+CSR, bc_compute from pinned host sources, bc_read into pinned host memory,
+bc_graph_destroy.  `--impl reference` times the CPU oracle (the plain
+single-threaded Brandes of oracle/) on a bounded sample of the same workload.
+
+With torchrun (N > 1) every rank runs the same workload size on its own
+seeded source sample (weak scaling; no collective on the data path), and
+rank 0 prints the line with the time of the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact-BC GTEPS (sources×edges/s), learned-batched vs plain GPU; % HBM roofline"
+UNIT = "GTEPS"
+WORKLOADS = {
+    "rmat18": "R-MAT scale 18 (262,144 vertices, edge factor 16, a=0.57 b=0.19 c=0.19 d=0.05), symmetrised, "
+              "deduplicated, int32 CSR, seed 2; 4096 uniform sources in bitset batches of 64",
+    "er4096": "Erdos-Renyi n=4096, p=8/4095, seed 1, all 4096 vertices as sources",
+    "grid1024": "1024x1024 4-neighbour grid, 5% edges removed, LCC, seed 3, 1024 uniform sources",
+    "rmat22": "R-MAT scale 22, edge factor 16, seed 5, 16,384 uniform sources",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="rmat18", choices=sorted(WORKLOADS))
+    ap.add_argument("--policy", default="auto")
+    ap.add_argument("--width", type=int, default=64)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=48, help="sources in the oracle's timed sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_workload(name, rank):
+    from paper_2008_05718_gb300 import graphgen as gg
+    g, S = gg.workload(name)
+    if rank > 0:  # weak scaling: same count, another seeded sample
+        S = gg.sample_sources(g.n, len(S), seed=10_000 + 97 * rank + len(S))
+    return g, S
+
+
+# ---- clocks -----------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    rows.append((float(p[1]), float(p[2]), p[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- reference arm: the CPU oracle -------------------------------------------
+
+def cpu_oracle_gteps(g, S, sample):
+    import oracle
+    oracle.build()
+    src = np.asarray(S[:sample], np.int32)
+    t = time.perf_counter()
+    oracle.bc_graph(g, src)
+    dt = time.perf_counter() - t
+    return len(src) * g.nnz / dt / 1e9, dt, len(src)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    g, S = load_workload(args.workload, 0)
+    sample = max(1, min(args.cpu_sample // 4, len(S)))
+    times = []
+    for i in range(args.warmup + args.steps):
+        _, dt, k = cpu_oracle_gteps(g, S[i * sample % len(S):], sample)
+        if i >= args.warmup:
+            times.append(dt)
+    value = args.steps * sample * g.nnz / sum(times) / 1e9
+    desc = f"{sample} sources per step of the {len(S)}-source list, full graph (n={g.n}, nnz={g.nnz})"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
+                                            "sources": len(S), "n": g.n, "nnz": g.nnz},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---- our arm -------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_from_profiles(kernel_kind, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_kind}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_2008_05718_gb300", "csrc", "bc_kernels.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != h:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_ours(args):
+    import torch
+    from paper_2008_05718_gb300 import _build, gbbc
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _build.build()
+    gbbc.load()
+    g, S = load_workload(args.workload, rank)
+    k = len(S)
+    stream = torch.cuda.current_stream(dev)
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    src = torch.from_numpy(S).to(dev)
+    out = torch.zeros(g.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    opts = dict(batch_width=args.width, policy=args.policy)
+
+    bc = gbbc.BC.from_csr(g.n, rp, col, stream=stream, **opts)
+
+    def step():
+        bc.reset()
+        bc.compute(src, stream=stream)
+        bc.read(out, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = bc.stats()["kernel_launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.summary()
+    launches = bc.stats()["kernel_launches"] - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps * k * g.nnz / total_s / 1e9
+
+    # ---- end to end through the C ABI with host buffers ----
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    src_h = torch.from_numpy(S).pin_memory()
+    out_h = torch.zeros(g.n, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with gbbc.BC.from_csr(g.n, rp_h, col_h, stream=stream, **opts) as h:
+            h.compute(src_h, stream=stream)
+            h.read(out_h, stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_val = k * g.nnz / e2e_s / 1e9 * world
+    h2d = (g.n + 1) * 4 + g.nnz * 4 + k * 4
+    d2h = g.n * 8
+
+    # ---- roofline of the dominant step kind (one traced step) ----
+    with gbbc.BC.from_csr(g.n, rp, col, stream=stream, flags=gbbc.GBBC_TRACE, **opts) as tb:
+        tb.compute(src, stream=stream)
+        tb.sync()
+        prof = tb.profile()
+    kind = max(prof, key=lambda x: prof[x]["ms"])
+    p = prof[kind]
+    peak, peak_src = measured_peaks()
+    achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] > 0 else 0.0
+    tr = traffic_from_profiles(kind, args.workload)
+    total_ms = sum(v["ms"] for v in prof.values())
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": tr, "kernel": kind, "launches_per_step": p["launches"],
+            "bytes_per_launch": p["bytes"] / max(p["launches"], 1), "ms_per_launch": p["ms"] / max(p["launches"], 1),
+            "share_of_step": p["ms"] / total_ms if total_ms else None, "peak_source": f"{peak_src} hbm_gbs (copy)",
+            "steps": {x: {"ms": round(v["ms"], 3), "GBps": (v["bytes"] / v["ms"] / 1e6) if v["ms"] else 0.0}
+                      for x, v in prof.items()}}
+
+    # ---- CPU baseline: the oracle on a bounded sample ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, dt, ks = cpu_oracle_gteps(g, S, min(args.cpu_sample, k))
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {ks} of the {k} sources, full graph; {dt:.1f} s on 1 core"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "sources": k,
+                           "n": g.n, "nnz": g.nnz, "batch_width": args.width, "policy": args.policy,
+                           "l2": "flushed between timed steps (512 MiB device write)"},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
+                "step_ms": [round(x, 3) for x in step_ms]}
+        print(json.dumps(line))
+    bc.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -64,7 +64,12 @@ enum gbbc_policy {
 enum gbbc_flags {
     GBBC_KEEP_STATE = 1u << 0, /* keep per-source dist/sigma of the last
                                   bc_compute for bc_read_source_state */
-    GBBC_TRACE = 1u << 1       /* record per-level features and times */
+    GBBC_TRACE = 1u << 1,      /* record per-level features and CUDA-event
+                                  times (bc_get_trace, bc_get_profile) */
+    GBBC_TRACE_BOTH = 1u << 2  /* with GBBC_TRACE: time both directions at
+                                  every forward level (the step is run top-down,
+                                  undone, then run bottom-up); results are
+                                  unchanged, only slower */
 };
 
 typedef struct gbbc_options {
@@ -174,6 +179,55 @@ typedef struct gbbc_stats {
 } gbbc_stats;
 
 gbbc_status bc_get_stats(const gbbc_graph* g, gbbc_stats* out);
+
+/*
+ * Per-level trace (GBBC_TRACE): one record per forward step of every batch,
+ * appended until bc_clear_trace.  A step at level l discovers level l+1.
+ * "lanes" count (vertex, source) pairs; times are CUDA-event milliseconds on
+ * the compute stream (-1 when not measured).
+ */
+typedef struct gbbc_level_trace {
+    int32_t batch;              /* batch index since the handle was created */
+    int32_t level;              /* l */
+    int32_t direction;          /* step run: 0 top-down push, 1 bottom-up pull */
+    int32_t active_lanes;       /* sources whose frontier is not empty */
+    int64_t n_range;            /* vertices of the batch's graph */
+    int64_t nnz_range;          /* CSR entries of the batch's graph */
+    int64_t frontier_vertices;  /* vertices at level l in some lane */
+    int64_t frontier_edges;     /* sum of their degrees */
+    int64_t frontier_lanes;     /* (vertex, lane) pairs at level l */
+    int64_t visited_lanes;      /* (vertex, lane) pairs at levels <= l */
+    int64_t visited_lane_edges; /* sum of degree over those pairs */
+    int64_t max_degree;         /* largest degree in the graph */
+    int64_t next_vertices;      /* vertices at level l+1 in some lane */
+    int64_t next_edges;         /* sum of their degrees */
+    int64_t scanned_edges;      /* CSR entries read by a bottom-up step */
+    float ms_push;              /* top-down discovery time */
+    float ms_pull;              /* bottom-up discovery time */
+    float ms_gather;            /* sigma gather of level l+1 */
+    float ms_backward;          /* backward step of level l+1 */
+} gbbc_level_trace;
+
+/* Copy up to max records into out; *count receives the number available. */
+gbbc_status bc_get_trace(const gbbc_graph* g, gbbc_level_trace* out, int64_t max, int64_t* count);
+gbbc_status bc_clear_trace(gbbc_graph* g);
+
+/*
+ * Per-step-kind profile (GBBC_TRACE): CUDA-event time and algorithmic bytes
+ * summed over all launches since the last bc_clear_trace.  Kinds: "push",
+ * "pull", "gather", "backward", "init".  Algorithmic bytes follow a
+ * compulsory-traffic model: each CSR row, mask word, sigma and coefficient
+ * the step needs is counted once per step.
+ */
+typedef struct gbbc_kernel_profile {
+    char name[32];
+    int64_t launches;  /* steps of this kind (each is one warp-per-row and one
+                          block-per-row kernel, two plus a filter for pull) */
+    double ms;         /* summed CUDA-event time */
+    double bytes;      /* summed algorithmic bytes */
+} gbbc_kernel_profile;
+
+gbbc_status bc_get_profile(const gbbc_graph* g, gbbc_kernel_profile* out, int32_t max, int32_t* count);
 
 #ifdef __cplusplus
 }

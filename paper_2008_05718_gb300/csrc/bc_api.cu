@@ -20,6 +20,7 @@ using namespace gbbc;
 
 extern "C" const char* bc_status_string(gbbc_status s);
 extern "C" void bc_graph_destroy(gbbc_graph* g);
+extern "C" gbbc_status bc_clear_trace(gbbc_graph* g);
 
 struct gbbc_graph {
     int device = 0;
@@ -39,6 +40,12 @@ struct gbbc_graph {
     size_t bytes = 0;
     gbbc_stats stats;
     cudaStream_t last_stream = nullptr;
+    // tracing (GBBC_TRACE)
+    std::vector<gbbc_level_trace> trace;
+    gbbc_kernel_profile prof[5];
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    long long batch_counter = 0;
     // kept per-source state of the last bc_compute
     int32_t* k_dist = nullptr;
     uint64_t* k_sigma = nullptr;
@@ -282,12 +289,72 @@ bool choose_pull(const gbbc_graph* g, DirState& d, int level, long long m_f, lon
     return d.pull;
 }
 
+enum ProfKind { PK_PUSH = 0, PK_PULL = 1, PK_GATHER = 2, PK_BWD = 3, PK_INIT = 4, PK_COUNT = 5 };
+const char* kProfNames[PK_COUNT] = {"push", "pull", "gather", "backward", "init"};
+
+// CUDA events around traced steps, resolved at the next host sync.
+struct Timed {
+    int kind;
+    cudaEvent_t a, b;
+    long long rec;   // trace record index, or -1
+    int field;       // 0 push, 1 pull, 2 gather, 3 backward, -1 none
+    double bytes;
+    bool count;      // counts in the profile (an undone probe step does not)
+};
+
+cudaEvent_t ev_get(gbbc_graph* g) {
+    if (g->ev_used == g->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        g->ev_pool.push_back(e);
+    }
+    return g->ev_pool[g->ev_used++];
+}
+
+gbbc_status resolve(gbbc_graph* g, std::vector<Timed>& pend) {
+    for (const Timed& t : pend) {
+        float ms = 0.f;
+        CK(g, cudaEventElapsedTime(&ms, t.a, t.b));
+        if (t.count) {
+            g->prof[t.kind].launches += 1;
+            g->prof[t.kind].ms += ms;
+            g->prof[t.kind].bytes += t.bytes;
+        }
+        if (t.rec >= 0 && t.rec < (long long)g->trace.size()) {
+            gbbc_level_trace& r = g->trace[t.rec];
+            if (t.field == 0) r.ms_push = ms;
+            if (t.field == 1) r.ms_pull = ms;
+            if (t.field == 2) r.ms_gather = ms;
+            if (t.field == 3) r.ms_backward = ms;
+        }
+    }
+    pend.clear();
+    g->ev_used = 0;
+    return GBBC_OK;
+}
+
+inline double dmin(double a, double b) { return a < b ? a : b; }
+
 gbbc_status run_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
     Slot& s = g->slot;
     Csr c{g->n, g->nnz, g->d_row_ptr, g->d_col};
     const int32_t lo = b.lo, hi = b.hi;
     const size_t rn = (size_t)(hi - lo);
     const int hd = g->opt.heavy_degree;
+    const bool tr = (g->opt.flags & GBBC_TRACE) != 0;
+    const bool both = tr && (g->opt.flags & GBBC_TRACE_BOTH) != 0;
+    std::vector<Timed> pend;
+    const long long batch_id = g->batch_counter++;
+    auto mark = [&](cudaEvent_t* e) -> gbbc_status {
+        *e = nullptr;
+        if (!tr) return GBBC_OK;
+        *e = ev_get(g);
+        if (!*e) return fail(g, GBBC_ERR_CUDA, "cudaEventCreate failed");
+        CK(g, cudaEventRecord(*e, st));
+        return GBBC_OK;
+    };
+    cudaEvent_t e0, e1;
+    CKS(mark(&e0));
     // ---- batch init (vertex range only) ----
     CK(g, cudaMemsetAsync(s.vis + lo, 0, rn * sizeof(u64), st));
     CK(g, cudaMemsetAsync(s.nx + lo, 0, rn * sizeof(u64), st));
@@ -299,29 +366,79 @@ gbbc_status run_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
     std::vector<int32_t> distinct(b.src, b.src + b.nsrc);
     std::sort(distinct.begin(), distinct.end());
     distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
-    long long nq0 = (long long)distinct.size();
-    long long m_f = 0;
-    for (int32_t v : distinct) m_f += g->h_row_ptr[v + 1] - g->h_row_ptr[v];
+    const long long nq0 = (long long)distinct.size();
+    long long deg0 = 0, lane_deg0 = 0;
+    for (int32_t v : distinct) deg0 += g->h_row_ptr[v + 1] - g->h_row_ptr[v];
+    for (int j = 0; j < b.nsrc; ++j) lane_deg0 += g->h_row_ptr[b.src[j] + 1] - g->h_row_ptr[b.src[j]];
     std::memset(s.hctr, 0, sizeof(Counters));
     s.hctr->qtail = (unsigned long long)nq0;
     CK(g, cudaMemcpyAsync(s.ctr, s.hctr, sizeof(Counters), cudaMemcpyHostToDevice, st));
     launch_seed(s, b.nsrc, st);
     g->stats.kernel_launches++;
     CK(g, cudaGetLastError());
+    CKS(mark(&e1));
+    if (tr) pend.push_back({PK_INIT, e0, e1, -1, -1, (double)rn * (8 * 3 + 32), true});
 
-    std::vector<long long> off = {0, nq0};
-    long long nnz_range = (long long)g->h_row_ptr[hi] - g->h_row_ptr[lo];
-    long long n_range = hi - lo;
+    // per-level sizes: entries, degree sum, (vertex, lane) pairs, pairs * degree
+    std::vector<long long> off = {0, nq0}, nv = {nq0}, ne = {deg0}, nl = {b.nsrc}, nle = {lane_deg0};
+    std::vector<long long> trace_rec;  // trace record of each level's step
+    const long long nnz_range = (long long)g->h_row_ptr[hi] - g->h_row_ptr[lo];
+    const long long n_range = hi - lo;
+    const double nr = (double)n_range;
+    long long max_deg = 0;
     u64 lanes = (b.nsrc == 64) ? ~0ull : ((1ull << b.nsrc) - 1ull);
     DirState dir;
     int level = 0;
-    const size_t step_bytes = offsetof(Counters, err) - offsetof(Counters, heavy);
+    const size_t disc_off = offsetof(Counters, heavy), disc_bytes = offsetof(Counters, err) - disc_off;
+    const size_t gath_off = offsetof(Counters, lane_sum), gath_bytes = offsetof(Counters, medium) - gath_off;
     for (;;) {
-        long long q_lo = off[level], q_hi = off[level + 1];
-        long long n_f = q_hi - q_lo;
-        bool pull = choose_pull(g, dir, level, m_f, n_f, n_range, nnz_range);
+        const long long q_lo = off[level], q_hi = off[level + 1];
+        const long long m_f = ne[level];
+        bool pull = choose_pull(g, dir, level, m_f, nv[level], n_range, nnz_range);
         dir.explored += m_f;
-        CK(g, cudaMemsetAsync(&s.ctr->heavy, 0, step_bytes, st));
+        long long rec = -1;
+        if (tr) {
+            gbbc_level_trace r;
+            std::memset(&r, 0, sizeof(r));
+            r.batch = (int32_t)batch_id;
+            r.level = level;
+            r.direction = pull ? 1 : 0;
+            r.active_lanes = __builtin_popcountll(lanes);
+            r.n_range = n_range;
+            r.nnz_range = nnz_range;
+            r.frontier_vertices = nv[level];
+            r.frontier_edges = ne[level];
+            r.frontier_lanes = nl[level];
+            long long vl = 0, vle = 0;
+            for (int i = 0; i <= level; ++i) { vl += nl[i]; vle += nle[i]; }
+            r.visited_lanes = vl;
+            r.visited_lane_edges = vle;
+            if (max_deg == 0)
+                for (int32_t v = lo; v < hi; ++v) max_deg = std::max<long long>(max_deg, g->h_row_ptr[v + 1] - g->h_row_ptr[v]);
+            r.max_degree = max_deg;
+            r.ms_push = r.ms_pull = r.ms_gather = r.ms_backward = -1.f;
+            rec = (long long)g->trace.size();
+            g->trace.push_back(r);
+            trace_rec.push_back(rec);
+        }
+        // probe the direction not taken, then undo it (GBBC_TRACE_BOTH)
+        if (both) {
+            CK(g, cudaMemsetAsync((char*)s.ctr + disc_off, 0, disc_bytes, st));
+            CKS(mark(&e0));
+            if (!pull) launch_pull(c, s, lo, hi, lanes, level, hd, g->nsm, st);
+            else launch_push(c, s, q_lo, q_hi, level, hd, g->nsm, st);
+            CKS(mark(&e1));
+            pend.push_back({pull ? PK_PUSH : PK_PULL, e0, e1, rec, pull ? 0 : 1, 0.0, false});
+            CK(g, cudaGetLastError());
+            CK(g, cudaMemcpyAsync(s.hctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+            CK(g, cudaStreamSynchronize(st));
+            launch_undo(s, q_hi, (long long)s.hctr->qtail, st);
+            unsigned long long rewind = (unsigned long long)q_hi;
+            CK(g, cudaMemcpyAsync(&s.ctr->qtail, &rewind, sizeof(rewind), cudaMemcpyHostToDevice, st));
+            CK(g, cudaStreamSynchronize(st));
+        }
+        CK(g, cudaMemsetAsync((char*)s.ctr + disc_off, 0, disc_bytes, st));
+        CKS(mark(&e0));
         if (pull) {
             launch_pull(c, s, lo, hi, lanes, level, hd, g->nsm, st);
             g->stats.levels_pull++;
@@ -331,21 +448,50 @@ gbbc_status run_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
             g->stats.levels_push++;
             g->stats.kernel_launches += 2;
         }
+        CKS(mark(&e1));
         CK(g, cudaGetLastError());
         CK(g, cudaMemcpyAsync(s.hctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
         CK(g, cudaStreamSynchronize(st));
         if (s.hctr->err)
             return fail(g, GBBC_ERR_CAPACITY, "queue capacity exceeded in the forward phase (flags %u)",
                         s.hctr->err);
-        long long new_hi = (long long)s.hctr->qtail;
-        if (new_hi == q_hi) break;  // no vertex reached at level+1
+        if (level >= 1) {  // lane statistics of level `level` (from its gather)
+            nl.push_back((long long)s.hctr->lane_sum);
+            nle.push_back((long long)s.hctr->lane_esum);
+        }
+        const long long new_hi = (long long)s.hctr->qtail;
+        const long long new_n = new_hi - q_hi, new_e = (long long)s.hctr->edge_sum;
+        if (tr) {
+            gbbc_level_trace& r = g->trace[rec];
+            r.next_vertices = new_n;
+            r.next_edges = new_e;
+            r.scanned_edges = pull ? (long long)s.hctr->scanned : 0;
+            double bytes = pull ? 8.0 * nr + 4.0 * (double)s.hctr->scanned +
+                                      16.0 * dmin((double)s.hctr->scanned, nr) + 20.0 * (double)new_n
+                                : 20.0 * (double)nv[level] + 4.0 * (double)m_f + 8.0 * dmin((double)m_f, nr) +
+                                      20.0 * (double)new_n;
+            pend.push_back({pull ? PK_PULL : PK_PUSH, e0, e1, rec, pull ? 1 : 0, bytes, true});
+            CKS(resolve(g, pend));
+        }
+        if (new_n == 0) break;  // no vertex reached at level+1
         off.push_back(new_hi);
-        m_f = (long long)s.hctr->edge_sum;
+        nv.push_back(new_n);
+        ne.push_back(new_e);
         lanes = s.hctr->lanes;
-        CK(g, cudaMemsetAsync(&s.ctr->heavy, 0, step_bytes, st));
+        CK(g, cudaMemsetAsync((char*)s.ctr + gath_off, 0, gath_bytes, st));
+        CKS(mark(&e0));
         launch_fwd_gather(c, s, q_hi, new_hi, level, hd, g->nsm, st);
+        CKS(mark(&e1));
         g->stats.kernel_launches += 2;
         CK(g, cudaGetLastError());
+        if (tr) {
+            // sigma reads of level `level` + writes of level+1 (lane counts of
+            // level+1 arrive with the next read-back: bytes use level's count
+            // as the estimate and are corrected below)
+            double bytes = 68.0 * (double)new_n + 4.0 * (double)new_e + 16.0 * dmin((double)new_e, nr) +
+                           8.0 * (double)nl[level];
+            pend.push_back({PK_GATHER, e0, e1, rec, 2, bytes, true});
+        }
         ++level;
     }
     const int nlev = level + 1;  // levels 0 .. level
@@ -356,6 +502,8 @@ gbbc_status run_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
     if (s.hctr->carry)
         return fail(g, GBBC_ERR_CAPACITY,
                     "a shortest-path count reached 2^64 and the wide sigma format is not available");
+    if (tr)  // sigma writes of each gathered level
+        for (int l = 1; l < nlev; ++l) g->prof[PK_GATHER].bytes += 8.0 * (double)nl[l];
     // ---- kept state for parity checks ----
     if (g->k_dist) {
         for (int l = 0; l < nlev; ++l)
@@ -366,11 +514,24 @@ gbbc_status run_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
     }
     // ---- backward phase: levels nlev-1 .. 1 ----
     for (int l = nlev - 1; l >= 1; --l) {
-        CK(g, cudaMemsetAsync(&s.ctr->heavy, 0, step_bytes, st));
+        CK(g, cudaMemsetAsync(&s.ctr->heavy, 0, sizeof(unsigned long long), st));
+        CKS(mark(&e0));
         launch_bwd(c, s, g->d_bc, off[l], off[l + 1], l, hd, g->nsm, st);
+        CKS(mark(&e1));
         g->stats.kernel_launches += 2;
+        if (tr) {
+            double succ_lanes = (l + 1 < nlev) ? (double)nl[l + 1] : 0.0;
+            double bytes = 52.0 * (double)nv[l] + 4.0 * (double)ne[l] + 16.0 * dmin((double)ne[l], nr) +
+                           8.0 * succ_lanes + 16.0 * (double)nl[l];
+            long long rec = (l - 1 < (int)trace_rec.size()) ? trace_rec[l - 1] : -1;
+            pend.push_back({PK_BWD, e0, e1, rec, 3, bytes, true});
+        }
     }
     CK(g, cudaGetLastError());
+    if (tr) {
+        CK(g, cudaStreamSynchronize(st));
+        CKS(resolve(g, pend));
+    }
     g->stats.batches++;
     g->stats.sources += b.nsrc;
     return GBBC_OK;
@@ -433,6 +594,7 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
 }
 
 gbbc_status finish_create(gbbc_graph* g, cudaStream_t st) {
+    bc_clear_trace(g);
     CKS(dalloc_t(g, &g->d_bc, (size_t)std::max<int32_t>(g->n, 1)));
     CK(g, cudaMemsetAsync(g->d_bc, 0, (size_t)std::max<int32_t>(g->n, 1) * sizeof(double), st));
     g->stats.batch_width = g->opt.batch_width == 0 ? 64 : g->opt.batch_width;
@@ -632,6 +794,7 @@ void bc_graph_destroy(gbbc_graph* g) {
     for (auto& a : g->allocs) cudaFree(a.first);
     g->allocs.clear();
     if (g->slot.hctr) cudaFreeHost(g->slot.hctr);
+    for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
     delete g;
 }
 
@@ -651,6 +814,31 @@ const char* bc_status_string(gbbc_status s) {
 gbbc_status bc_last_error_detail(const gbbc_graph* g, char* buf, size_t len) {
     if (!buf || len == 0) return GBBC_ERR_INVALID;
     std::snprintf(buf, len, "%s", g ? g->err.c_str() : tl_create_err.c_str());
+    return GBBC_OK;
+}
+
+gbbc_status bc_get_trace(const gbbc_graph* g, gbbc_level_trace* out, int64_t max, int64_t* count) {
+    if (!g || (max > 0 && !out)) return GBBC_ERR_INVALID;
+    long long n = (long long)g->trace.size();
+    if (count) *count = n;
+    for (long long i = 0; i < n && i < max; ++i) out[i] = g->trace[i];
+    return GBBC_OK;
+}
+
+gbbc_status bc_clear_trace(gbbc_graph* g) {
+    if (!g) return GBBC_ERR_INVALID;
+    g->trace.clear();
+    for (int k = 0; k < PK_COUNT; ++k) {
+        std::memset(&g->prof[k], 0, sizeof(gbbc_kernel_profile));
+        std::snprintf(g->prof[k].name, sizeof(g->prof[k].name), "%s", kProfNames[k]);
+    }
+    return GBBC_OK;
+}
+
+gbbc_status bc_get_profile(const gbbc_graph* g, gbbc_kernel_profile* out, int32_t max, int32_t* count) {
+    if (!g || (max > 0 && !out)) return GBBC_ERR_INVALID;
+    if (count) *count = PK_COUNT;
+    for (int k = 0; k < PK_COUNT && k < max; ++k) out[k] = g->prof[k];
     return GBBC_OK;
 }
 

@@ -37,15 +37,20 @@ struct __align__(16) MaskTag {
     int32_t pad;
 };
 
-// Counters of one batch, written by kernels, read back by the host.
+// Counters of one batch, written by kernels, read back by the host once per
+// level.  Field order matters: the host zeroes [lane_sum, heavy] before a
+// gather step and [heavy, lanes] before a discovery step.
 struct __align__(16) Counters {
-    unsigned long long qtail;    // next free position in the entry queue
-    unsigned long long heavy;    // rows deferred to the block-per-row kernel
-    unsigned long long medium;   // rows deferred to the warp-per-row pull kernel
-    unsigned long long edge_sum; // sum of degrees of the newly queued vertices
-    u64 lanes;                   // OR of the masks of the newly queued vertices
-    unsigned err;                // bit 0: queue overflow, bit 1: row list overflow
-    unsigned carry;              // some sigma reached 2^64 in this batch
+    unsigned long long qtail;     // next free position in the entry queue
+    unsigned long long lane_sum;  // gather: sum of popc(mask) of its entries
+    unsigned long long lane_esum; // gather: sum of popc(mask) * degree
+    unsigned long long heavy;     // rows deferred to the block-per-row kernel
+    unsigned long long medium;    // rows deferred to the warp-per-row pull kernel
+    unsigned long long edge_sum;  // discovery: sum of degrees of new vertices
+    unsigned long long scanned;   // discovery: CSR entries read by a pull step
+    u64 lanes;                    // discovery: OR of the lanes reaching them
+    unsigned err;                 // bit 0: queue overflow, bit 1: row list overflow
+    unsigned carry;               // some sigma reached 2^64 in this batch
 };
 
 // Device state of one batch slot (sized for n vertices, 64 lanes).
@@ -88,6 +93,7 @@ void launch_keep_dist(const Slot& s, long long q_lo, long long q_hi, int level, 
                       long long first_src, int nsrc, cudaStream_t st);
 void launch_keep_sigma(const Slot& s, int32_t lo, int32_t hi, uint64_t* sigma, uint8_t* ovf, long long n_total,
                        long long first_src, int nsrc, cudaStream_t st);
+void launch_undo(const Slot& s, long long q_lo, long long q_hi, cudaStream_t st);
 void launch_validate(const Csr& g, int32_t* flags, cudaStream_t st);
 void launch_fill_i32(int32_t* p, long long count, int32_t value, cudaStream_t st);
 void launch_offset_copy(const int32_t* src, int32_t* dst, long long count, int32_t add, cudaStream_t st);

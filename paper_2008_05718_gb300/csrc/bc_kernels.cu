@@ -103,17 +103,22 @@ void launch_seed(const Slot& s, int nsrc, cudaStream_t st) { k_seed<<<1, kLanes,
 // of degrees of newly queued vertices and the OR of the lanes reaching them.
 struct StepStats {
     unsigned long long esum;
+    unsigned long long scanned;
     u64 lanes;
 };
 
 __device__ __forceinline__ void flush_stats(const Slot& s, StepStats st) {
     // all 32 threads of the warp call this
-    unsigned long long e = st.esum;
+    unsigned long long e = st.esum, c = st.scanned;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) e += __shfl_xor_sync(FULL, e, o);
+    for (int o = 16; o >= 1; o >>= 1) {
+        e += __shfl_xor_sync(FULL, e, o);
+        c += __shfl_xor_sync(FULL, c, o);
+    }
     u64 l = warp_or64(st.lanes);
-    if ((threadIdx.x & 31) == 0 && (e | l)) {
+    if ((threadIdx.x & 31) == 0 && (e | l | c)) {
         atomicAdd(&s.ctr->edge_sum, e);
+        atomicAdd(&s.ctr->scanned, c);
         atomicOr(&s.ctr->lanes, l);
     }
 }
@@ -140,7 +145,7 @@ __device__ __forceinline__ void push_row(const Csr& g, const Slot& s, u64 m, int
 
 __global__ void k_push(Csr g, Slot s, long long q_lo, long long q_hi, int heavy_deg) {
     const int lane = threadIdx.x & 31;
-    StepStats stats = {0ull, 0ull};
+    StepStats stats = {0ull, 0ull, 0ull};
     for (long long e = q_lo + gwarp(); e < q_hi; e += nwarps()) {
         int32_t v = s.qv[e];
         u64 m = s.qm[e];
@@ -160,7 +165,7 @@ __global__ void k_push(Csr g, Slot s, long long q_lo, long long q_hi, int heavy_
 
 __global__ void k_push_heavy(Csr g, Slot s) {
     const long long cnt = (long long)s.ctr->heavy;
-    StepStats stats = {0ull, 0ull};
+    StepStats stats = {0ull, 0ull, 0ull};
     for (long long h = blockIdx.x; h < cnt; h += gridDim.x) {
         long long e = s.heavy[h];
         int32_t v = s.qv[e];
@@ -189,7 +194,7 @@ __global__ void k_pull_thread(Csr g, Slot s, int32_t lo, int32_t hi, u64 lanes, 
                               int32_t* medium, unsigned long long* n_medium) {
     const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    StepStats stats = {0ull, 0ull};
+    StepStats stats = {0ull, 0ull, 0ull};
     for (long long base = (long long)lo + (long long)blockIdx.x * blockDim.x; base < hi; base += stride) {
         int32_t w = (int32_t)(base + threadIdx.x);
         u64 u = 0;
@@ -207,6 +212,7 @@ __global__ void k_pull_thread(Csr g, Slot s, int32_t lo, int32_t hi, u64 lanes, 
         u64 f = 0;
         if (u) {
             for (int32_t p = beg; p < end; ++p) {
+                ++stats.scanned;
                 int32_t v = __ldg(g.col + p);
                 MaskTag t = F[v];
                 if (t.tag == level) {
@@ -234,7 +240,7 @@ __global__ void k_pull_medium(Csr g, Slot s, u64 lanes, int level, const int32_t
     const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
     const int lane = threadIdx.x & 31;
     const long long cnt = (long long)*n_medium;
-    StepStats stats = {0ull, 0ull};
+    StepStats stats = {0ull, 0ull, 0ull};
     for (long long i = gwarp(); i < cnt; i += nwarps()) {
         int32_t w = medium[i];
         u64 u = ~s.vis[w] & lanes;
@@ -243,6 +249,7 @@ __global__ void k_pull_medium(Csr g, Slot s, u64 lanes, int level, const int32_t
         for (int32_t base = beg; base < end; base += kWarp) {
             int32_t p = base + lane;
             if (p < end) {
+                ++stats.scanned;
                 MaskTag t = F[__ldg(g.col + p)];
                 if (t.tag == level) f |= t.mask;
             }
@@ -266,13 +273,14 @@ __global__ void k_pull_heavy(Csr g, Slot s, u64 lanes, int level) {
     __shared__ u64 part[kHeavyBlock / kWarp];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const long long cnt = (long long)s.ctr->heavy;
-    StepStats stats = {0ull, 0ull};
+    StepStats stats = {0ull, 0ull, 0ull};
     for (long long h = blockIdx.x; h < cnt; h += gridDim.x) {
         int32_t w = s.heavy[h];
         u64 u = ~s.vis[w] & lanes;
         int32_t beg = g.row_ptr[w], end = g.row_ptr[w + 1];
         u64 f = 0;
         for (int32_t p = beg + threadIdx.x; p < end; p += blockDim.x) {
+            ++stats.scanned;
             MaskTag t = F[__ldg(g.col + p)];
             if (t.tag == level) f |= t.mask;
         }
@@ -292,7 +300,7 @@ __global__ void k_pull_heavy(Csr g, Slot s, u64 lanes, int level) {
         }
         __syncthreads();
     }
-    if (wid == 0) flush_stats(s, stats);
+    flush_stats(s, stats);
 }
 
 void launch_pull(const Csr& g, const Slot& s, int32_t lo, int32_t hi, u64 lanes, int level, int heavy_deg, int nsm,
@@ -372,6 +380,7 @@ __global__ void k_fwd_gather(Csr g, Slot s, long long q_lo, long long q_hi, int 
     const int lane = threadIdx.x & 31;
     const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
     MaskTag* Fn = s.F + (size_t)((level + 1) & 1) * s.n;
+    unsigned long long lsum = 0, lesum = 0;
     for (long long e = q_lo + gwarp(); e < q_hi; e += nwarps()) {
         int32_t w = s.qv[e];
         u64 m = s.nx[w];
@@ -386,6 +395,9 @@ __global__ void k_fwd_gather(Csr g, Slot s, long long q_lo, long long q_hi, int 
             t.tag = level + 1;
             t.pad = 0;
             Fn[w] = t;
+            unsigned pc = (unsigned)__popcll(m);
+            lsum += pc;
+            lesum += (unsigned long long)pc * (unsigned long long)(end - beg);
         }
         if (end - beg > heavy_deg) {
             if (lane == 0) {
@@ -398,6 +410,10 @@ __global__ void k_fwd_gather(Csr g, Slot s, long long q_lo, long long q_hi, int 
         GatherAcc acc = {0ull, 0ull, 0u, 0u};
         fwd_gather_row<1>(g, s, F, level, m, beg, end, 0, acc);
         fwd_store(s, w, m, acc);
+    }
+    if (lane == 0 && lsum) {
+        atomicAdd(&s.ctr->lane_sum, lsum);
+        atomicAdd(&s.ctr->lane_esum, lesum);
     }
 }
 
@@ -602,6 +618,20 @@ void launch_keep_sigma(const Slot& s, int32_t lo, int32_t hi, uint64_t* sigma, u
                        long long first_src, int nsrc, cudaStream_t st) {
     if (hi <= lo || nsrc <= 0) return;
     k_keep_sigma<<<1216, 256, 0, st>>>(s, lo, hi, sigma, ovf, n_total, first_src, nsrc);
+}
+
+// ---------------------------------------------------------------------------
+// Undo a discovery step (used to time both directions at one level): the
+// vertices queued in [q_lo, q_hi) get nx cleared; the host rewinds qtail.
+__global__ void k_undo(Slot s, long long q_lo, long long q_hi) {
+    for (long long e = q_lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; e < q_hi;
+         e += (long long)gridDim.x * blockDim.x)
+        s.nx[s.qv[e]] = 0ull;
+}
+
+void launch_undo(const Slot& s, long long q_lo, long long q_hi, cudaStream_t st) {
+    if (q_hi <= q_lo) return;
+    k_undo<<<1216, 256, 0, st>>>(s, q_lo, q_hi);
 }
 
 // ---------------------------------------------------------------------------

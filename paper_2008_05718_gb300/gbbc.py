@@ -23,11 +23,12 @@ GBBC_OK, GBBC_ERR_INVALID, GBBC_ERR_OOM, GBBC_ERR_CUDA, GBBC_ERR_TIMEOUT, GBBC_E
 POLICY = {"auto": 0, "beamer": 1, "learned": 2, "push": 3, "pull": 4}
 GBBC_KEEP_STATE = 1
 GBBC_TRACE = 2
+GBBC_TRACE_BOTH = 4
 
 # every symbol include/gbbc.h declares
 EXPORTS = ("bc_options_init", "bc_graph_create", "bc_graph_create_multi", "bc_compute", "bc_compute_multi",
            "bc_read", "bc_read_source_state", "bc_reset", "bc_sync", "bc_graph_destroy", "bc_status_string",
-           "bc_last_error_detail", "bc_get_stats")
+           "bc_last_error_detail", "bc_get_stats", "bc_get_trace", "bc_clear_trace", "bc_get_profile")
 
 
 class gbbc_options(ctypes.Structure):
@@ -44,6 +45,22 @@ class gbbc_stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class gbbc_level_trace(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int32), ("level", ctypes.c_int32), ("direction", ctypes.c_int32),
+                ("active_lanes", ctypes.c_int32), ("n_range", ctypes.c_int64), ("nnz_range", ctypes.c_int64),
+                ("frontier_vertices", ctypes.c_int64), ("frontier_edges", ctypes.c_int64),
+                ("frontier_lanes", ctypes.c_int64), ("visited_lanes", ctypes.c_int64),
+                ("visited_lane_edges", ctypes.c_int64), ("max_degree", ctypes.c_int64),
+                ("next_vertices", ctypes.c_int64), ("next_edges", ctypes.c_int64),
+                ("scanned_edges", ctypes.c_int64), ("ms_push", ctypes.c_float), ("ms_pull", ctypes.c_float),
+                ("ms_gather", ctypes.c_float), ("ms_backward", ctypes.c_float)]
+
+
+class gbbc_kernel_profile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 class GbbcError(RuntimeError):
@@ -78,6 +95,9 @@ def load():
             "bc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "bc_last_error_detail": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
             "bc_get_stats": (ctypes.c_int, [vp, P(gbbc_stats)]),
+            "bc_get_trace": (ctypes.c_int, [vp, P(gbbc_level_trace), i64, P(i64)]),
+            "bc_clear_trace": (ctypes.c_int, [vp]),
+            "bc_get_profile": (ctypes.c_int, [vp, P(gbbc_kernel_profile), i32, P(i32)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -251,6 +271,34 @@ def bc_get_stats(handle) -> dict:
     return s.as_dict()
 
 
+TRACE_FIELDS = [f for f, _ in gbbc_level_trace._fields_]
+
+
+def bc_get_trace(handle) -> dict:
+    """Per-level trace records as a dict of numpy arrays (one entry per field)."""
+    lib = load()
+    cnt = ctypes.c_int64()
+    _check(lib.bc_get_trace(handle, None, 0, ctypes.byref(cnt)), handle)
+    arr = (gbbc_level_trace * max(cnt.value, 1))()
+    _check(lib.bc_get_trace(handle, arr, cnt.value, ctypes.byref(cnt)), handle)
+    recs = arr[: cnt.value]
+    return {f: np.array([getattr(r, f) for r in recs]) for f in TRACE_FIELDS}
+
+
+def bc_clear_trace(handle):
+    _check(load().bc_clear_trace(handle), handle)
+
+
+def bc_get_profile(handle) -> dict:
+    """{kind: {"launches", "ms", "bytes"}} for the traced steps."""
+    lib = load()
+    arr = (gbbc_kernel_profile * 16)()
+    cnt = ctypes.c_int32()
+    _check(lib.bc_get_profile(handle, arr, 16, ctypes.byref(cnt)), handle)
+    return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes}
+            for i in range(cnt.value)}
+
+
 # ---- convenience object ------------------------------------------------------
 
 class BC:
@@ -306,6 +354,15 @@ class BC:
 
     def stats(self):
         return bc_get_stats(self.h)
+
+    def trace(self):
+        return bc_get_trace(self.h)
+
+    def profile(self):
+        return bc_get_profile(self.h)
+
+    def clear_trace(self):
+        bc_clear_trace(self.h)
 
     def close(self):
         if self.h:

@@ -192,3 +192,32 @@ def test_memory_limit_reports_oom(gb):
         with pytest.raises(gb.GbbcError) as e:
             bc.compute([0, 1, 2])
         assert e.value.status == gb.GBBC_ERR_OOM
+
+
+def test_trace_both_directions_keeps_results(gb):
+    g = gg.rmat(12, 16, seed=12)
+    S = gg.sample_sources(g.n, 100, seed=12)
+    want, ost = oracle.bc_graph(g, S, dump=(0, 99))
+    flags = gb.GBBC_KEEP_STATE | gb.GBBC_TRACE | gb.GBBC_TRACE_BOTH
+    with gb.BC.from_graph(g, flags=flags) as bc:
+        bc.compute(S)
+        assert_bc_close(bc.read(), want)
+        for i in (0, 99):
+            d, s, o = bc.source_state(i)
+            assert np.array_equal(d, ost[i].dist) and np.array_equal(s, ost[i].sigma)
+        tr = bc.trace()
+        prof = bc.profile()
+    assert len(tr["level"]) == bc_levels(ost, S, g) and np.all(tr["ms_push"] > 0) and np.all(tr["ms_pull"] > 0)
+    assert np.all(tr["ms_gather"][tr["next_vertices"] > 0] > 0)
+    for k in ("gather", "backward"):
+        assert prof[k]["launches"] > 0 and prof[k]["ms"] > 0 and prof[k]["bytes"] > 0
+
+
+def bc_levels(ost, S, g):
+    # forward steps = sum over batches of (deepest level + 1); recompute
+    # each batch's deepest level from the oracle
+    depths = []
+    for b in range(0, len(S), 64):
+        _, st = oracle.bc_graph(g, S[b:b + 64], dump=range(len(S[b:b + 64])))
+        depths.append(max(int(st[i].dist.max()) for i in st))
+    return sum(d + 1 for d in depths)
