@@ -229,6 +229,37 @@ typedef struct gbbc_kernel_profile {
 
 gbbc_status bc_get_profile(const gbbc_graph* g, gbbc_kernel_profile* out, int32_t max, int32_t* count);
 
+/*
+ * bc_compute_noalloc - BC of one small graph with no memory allocation.
+ * The paper has no counterpart; this entry point exists for callers that
+ * must not allocate memory themselves (code running under a pool allocator
+ * that owns the whole device, plug-in hosts whose allocator may not be
+ * bypassed, real-time loops that cannot afford cudaMalloc's implicit
+ * synchronisation).  It calls no cudaMalloc/cudaFree and no allocating
+ * library routine, and creates no handle.
+ *
+ * Working state lives in one static device array of the library, sized for
+ * GBBC_NOALLOC_MAX_VERTICES vertices (about 30 MiB); every GPU that loads
+ * libgbbc.so holds it until the process exits.  All calls share it: calls
+ * whose work overlaps on the GPU race and must be serialised by the caller.
+ * The array keeps the previous call's contents; each batch clears what must
+ * start at zero.  The first call on a device looks up the array's device
+ * address with cudaGetSymbolAddress (once per device, with that device
+ * current), so make it before any stream capture begins.
+ *
+ * Inputs: n <= GBBC_NOALLOC_MAX_VERTICES vertices; row_ptr[n+1], col[nnz]
+ * and bc_out[n] in DEVICE memory; sources[k] in HOST memory, each in [0, n).
+ * The dependencies of the k sources are ADDED into bc_out (zero it first for
+ * plain BC), in 64-source batches, always expanding top-down.  The call
+ * returns after the work has finished on `stream`.
+ * Errors: GBBC_ERR_CAPACITY when n exceeds GBBC_NOALLOC_MAX_VERTICES (or a
+ * shortest-path count reaches 2^64), GBBC_ERR_INVALID for bad arguments or
+ * pointers in the wrong memory, GBBC_ERR_CUDA.
+ */
+#define GBBC_NOALLOC_MAX_VERTICES 16384
+gbbc_status bc_compute_noalloc(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+                               const int32_t* sources, int64_t k, double* bc_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,188 @@
+// bc_compute_noalloc: exact Brandes BC for one small graph without any device
+// (or host heap) allocation, for callers that may not allocate memory
+// themselves -- for example code running inside a memory pool that owns the
+// whole device, a plug-in host whose allocator must not be bypassed, or a
+// real-time loop where cudaMalloc's implicit synchronisation is not allowed.
+//
+// All per-batch working state lives in one file-scope device array,
+// g_noalloc_scratch, sized for kNoallocMaxVertices vertices.  It is part of
+// the library image: every GPU that loads libgbbc.so holds it until the
+// process exits.  Every call shares it, so two calls whose work overlaps on
+// the GPU (different streams, or several host threads) race and give wrong
+// results; serialise them.  The array keeps the previous call's contents:
+// everything a batch needs at zero is cleared at the start of that batch.
+//
+// Host code cannot use the array's name as a device address (in host code
+// the symbol is a host-side stand-in), so the device address is looked up
+// with cudaGetSymbolAddress once per device, the first time a call runs on
+// that device with it current.  That first call should therefore come before
+// any stream capture begins.
+//
+// The kernels are the same ones bc_compute launches (64 sources per batch);
+// this path always expands top-down and adds into the caller's BC vector.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "bc_internal.cuh"
+
+using namespace gbbc;
+
+namespace {
+
+constexpr long long kNoallocMaxVertices = 16384;  // also in include/gbbc.h
+constexpr long long kNoallocQcap = kNoallocMaxVertices * kLanes + kLanes;
+
+constexpr long long align256(long long x) { return (x + 255) / 256 * 256; }
+
+// Byte offsets of the regions inside the scratch array.
+constexpr long long kOffVis = 0;
+constexpr long long kOffNx = kOffVis + align256(8 * kNoallocMaxVertices);
+constexpr long long kOffOvf = kOffNx + align256(8 * kNoallocMaxVertices);
+constexpr long long kOffF = kOffOvf + align256(8 * kNoallocMaxVertices);
+constexpr long long kOffSigma = kOffF + align256(2 * (long long)sizeof(MaskTag) * kNoallocMaxVertices);
+constexpr long long kOffCoef = kOffSigma + align256(8 * kLanes * kNoallocMaxVertices);
+constexpr long long kOffQv = kOffCoef + align256(8 * kLanes * kNoallocMaxVertices);
+constexpr long long kOffQm = kOffQv + align256(4 * kNoallocQcap);
+constexpr long long kOffHeavy = kOffQm + align256(8 * kNoallocQcap);
+constexpr long long kOffMedium = kOffHeavy + align256(4 * kNoallocMaxVertices);
+constexpr long long kOffCtr = kOffMedium + align256(4 * kNoallocMaxVertices);
+constexpr long long kOffSrc = kOffCtr + align256((long long)sizeof(Counters));
+constexpr long long kScratchBytes = kOffSrc + align256(4 * kLanes);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+unsigned char* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (set-up on the
+// first call per device).
+cudaError_t scratch_address(unsigned char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = (unsigned char*)p;
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+bool device_pointer(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+#define NA_CK(call)                               \
+    do {                                          \
+        if ((call) != cudaSuccess) return GBBC_ERR_CUDA; \
+    } while (0)
+
+extern "C" gbbc_status bc_compute_noalloc(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+                                          const int32_t* sources, int64_t k, double* bc_out, void* stream) {
+    if (n < 0 || nnz < 0 || nnz >= 0x7fffffffLL || k < 0) return GBBC_ERR_INVALID;
+    if (n > kNoallocMaxVertices) return GBBC_ERR_CAPACITY;
+    if (k == 0 || n == 0) return GBBC_OK;
+    if (!row_ptr || !col || !sources || !bc_out) return GBBC_ERR_INVALID;
+    if (!device_pointer(row_ptr) || !device_pointer(col) || !device_pointer(bc_out) || device_pointer(sources))
+        return GBBC_ERR_INVALID;
+    for (int64_t i = 0; i < k; ++i)
+        if (sources[i] < 0 || sources[i] >= n) return GBBC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* base = nullptr;
+    NA_CK(scratch_address(&base));
+    int dev = 0, nsm = 152;
+    NA_CK(cudaGetDevice(&dev));
+    NA_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+
+    Slot s;
+    s.n = n;
+    s.vis = (u64*)(base + kOffVis);
+    s.nx = (u64*)(base + kOffNx);
+    s.ovf = (u64*)(base + kOffOvf);
+    s.F = (MaskTag*)(base + kOffF);
+    s.sigma = (u64*)(base + kOffSigma);
+    s.coef = (double*)(base + kOffCoef);
+    s.qv = (int32_t*)(base + kOffQv);
+    s.qm = (u64*)(base + kOffQm);
+    s.heavy = (int32_t*)(base + kOffHeavy);
+    s.medium = (int32_t*)(base + kOffMedium);
+    s.ctr = (Counters*)(base + kOffCtr);
+    s.d_src = (int32_t*)(base + kOffSrc);
+    s.qcap = (long long)n * kLanes + kLanes;
+    // F is indexed [parity][n] with the stride of this graph's n
+    Csr c{n, (long long)nnz, row_ptr, col};
+    const int heavy_deg = 1024;
+    long long off[kNoallocMaxVertices + 2];  // level boundaries of a batch (on the stack)
+    const size_t disc_off = offsetof(Counters, heavy), disc_bytes = offsetof(Counters, err) - disc_off;
+    const size_t gath_off = offsetof(Counters, lane_sum), gath_bytes = offsetof(Counters, medium) - gath_off;
+
+    for (int64_t b0 = 0; b0 < k; b0 += kLanes) {
+        const int nsrc = (int)((k - b0) < kLanes ? (k - b0) : kLanes);
+        const int32_t* bsrc = sources + b0;
+        // clear what a batch needs at zero (the array keeps the last contents)
+        NA_CK(cudaMemsetAsync(s.vis, 0, (size_t)n * sizeof(u64), st));
+        NA_CK(cudaMemsetAsync(s.nx, 0, (size_t)n * sizeof(u64), st));
+        NA_CK(cudaMemsetAsync(s.ovf, 0, (size_t)n * sizeof(u64), st));
+        NA_CK(cudaMemsetAsync(s.F, 0xff, 2 * (size_t)n * sizeof(MaskTag), st));
+        NA_CK(cudaMemcpyAsync(s.d_src, bsrc, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        long long nq0 = 0;
+        for (int j = 0; j < nsrc; ++j) {
+            bool first = true;
+            for (int i = 0; i < j; ++i)
+                if (bsrc[i] == bsrc[j]) { first = false; break; }
+            nq0 += first;
+        }
+        Counters hc;
+        std::memset(&hc, 0, sizeof(hc));
+        hc.qtail = (unsigned long long)nq0;
+        NA_CK(cudaMemcpyAsync(s.ctr, &hc, sizeof(Counters), cudaMemcpyHostToDevice, st));
+        NA_CK(cudaStreamSynchronize(st));  // hc is on the stack
+        launch_seed(s, nsrc, st);
+        NA_CK(cudaGetLastError());
+        off[0] = 0;
+        off[1] = nq0;
+        int level = 0;
+        for (;;) {
+            const long long q_lo = off[level], q_hi = off[level + 1];
+            NA_CK(cudaMemsetAsync((char*)s.ctr + disc_off, 0, disc_bytes, st));
+            launch_push(c, s, q_lo, q_hi, level, heavy_deg, nsm, st);
+            NA_CK(cudaGetLastError());
+            NA_CK(cudaMemcpyAsync(&hc, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+            NA_CK(cudaStreamSynchronize(st));
+            if (hc.err) return GBBC_ERR_CAPACITY;
+            const long long new_hi = (long long)hc.qtail;
+            if (new_hi == q_hi) break;
+            if (level + 2 > kNoallocMaxVertices + 1) return GBBC_ERR_CAPACITY;
+            off[level + 2] = new_hi;
+            NA_CK(cudaMemsetAsync((char*)s.ctr + gath_off, 0, gath_bytes, st));
+            launch_fwd_gather(c, s, q_hi, new_hi, level, heavy_deg, nsm, st);
+            NA_CK(cudaGetLastError());
+            ++level;
+        }
+        const int nlev = level + 1;
+        NA_CK(cudaMemcpyAsync(&hc, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        NA_CK(cudaStreamSynchronize(st));
+        if (hc.err || hc.carry) return GBBC_ERR_CAPACITY;
+        for (int l = nlev - 1; l >= 1; --l) {
+            NA_CK(cudaMemsetAsync(&s.ctr->heavy, 0, sizeof(unsigned long long), st));
+            launch_bwd(c, s, bc_out, off[l], off[l + 1], l, heavy_deg, nsm, st);
+        }
+        NA_CK(cudaGetLastError());
+    }
+    NA_CK(cudaStreamSynchronize(st));
+    return GBBC_OK;
+}

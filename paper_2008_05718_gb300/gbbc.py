@@ -28,7 +28,9 @@ GBBC_TRACE_BOTH = 4
 # every symbol include/gbbc.h declares
 EXPORTS = ("bc_options_init", "bc_graph_create", "bc_graph_create_multi", "bc_compute", "bc_compute_multi",
            "bc_read", "bc_read_source_state", "bc_reset", "bc_sync", "bc_graph_destroy", "bc_status_string",
-           "bc_last_error_detail", "bc_get_stats", "bc_get_trace", "bc_clear_trace", "bc_get_profile")
+           "bc_last_error_detail", "bc_get_stats", "bc_get_trace", "bc_clear_trace", "bc_get_profile",
+           "bc_compute_noalloc")
+NOALLOC_MAX_VERTICES = 16384
 
 
 class gbbc_options(ctypes.Structure):
@@ -98,6 +100,7 @@ def load():
             "bc_get_trace": (ctypes.c_int, [vp, P(gbbc_level_trace), i64, P(i64)]),
             "bc_clear_trace": (ctypes.c_int, [vp]),
             "bc_get_profile": (ctypes.c_int, [vp, P(gbbc_kernel_profile), i32, P(i32)]),
+            "bc_compute_noalloc": (ctypes.c_int, [i32, i64, vp, vp, vp, i64, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -297,6 +300,20 @@ def bc_get_profile(handle) -> dict:
     _check(lib.bc_get_profile(handle, arr, 16, ctypes.byref(cnt)), handle)
     return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes}
             for i in range(cnt.value)}
+
+
+def bc_compute_noalloc(n, nnz, row_ptr, col, sources, bc_out, stream=None):
+    """Add the BC dependencies of `sources` (host int32) into bc_out (device
+    float64[n]) for the CSR in device memory, without allocating anything
+    in the library: for callers that may not allocate memory (see the C
+    header for the shared static scratch and its limits)."""
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    rp, k1 = _ptr(row_ptr)
+    cl, k2 = _ptr(col)
+    out, k3 = _ptr(bc_out)
+    st = load().bc_compute_noalloc(int(n), int(nnz), rp, cl, src.ctypes.data, len(src), out, _stream(stream))
+    if st != GBBC_OK:
+        raise GbbcError(st, "bc_compute_noalloc")
 
 
 # ---- convenience object ------------------------------------------------------
