@@ -239,7 +239,7 @@ gbbc_status bc_get_profile(const gbbc_graph* g, gbbc_kernel_profile* out, int32_
  * library routine, and creates no handle.
  *
  * Working state lives in one static device array of the library, sized for
- * GBBC_NOALLOC_MAX_VERTICES vertices (about 30 MiB); every GPU that loads
+ * GBBC_NOALLOC_MAX_VERTICES vertices (about 48 MiB); every GPU that loads
  * libgbbc.so holds it until the process exits.  All calls share it: calls
  * whose work overlaps on the GPU race and must be serialised by the caller.
  * The array keeps the previous call's contents; each batch clears what must

@@ -31,7 +31,9 @@ struct gbbc_graph {
     int32_t* d_col = nullptr;
     std::vector<int32_t> h_row_ptr;  // host copy for scheduling decisions
     std::vector<long long> goff;     // graph vertex offsets (count + 1)
-    double* d_bc = nullptr;
+    u64* d_bc = nullptr;             // [2n] BC in 128-bit fixed point (units 2^-64)
+    double* d_bc_out = nullptr;      // [n] staging for bc_read into host memory
+    bool wide_sticky = false;        // batches start in the wide sigma format
     Slot slot;
     bool slot_ready = false;
     gbbc_options opt;
@@ -245,16 +247,43 @@ gbbc_status alloc_slot(gbbc_graph* g) {
     CKS(dalloc_t(g, &s.ovf, n));
     CKS(dalloc_t(g, &s.F, 2 * n));
     CKS(dalloc_t(g, &s.sigma, n * kLanes));
-    CKS(dalloc_t(g, &s.coef, n * kLanes));
+    CKS(dalloc_t(g, &s.psi, n * kLanes));
     CKS(dalloc_t(g, &s.qv, (size_t)qcap));
     CKS(dalloc_t(g, &s.qm, (size_t)qcap));
     CKS(dalloc_t(g, &s.heavy, n));
     CKS(dalloc_t(g, &s.medium, n));
+    // heavy rows: exact bounds from the degrees (a row appears at most once per step)
+    long long hcap = 1, tcap = 1;
+    for (int32_t v = 0; v < g->n; ++v) {
+        long long d = (long long)g->h_row_ptr[v + 1] - g->h_row_ptr[v];
+        if (d > g->opt.heavy_degree) {
+            hcap += 1;
+            tcap += (d + kChunk - 1) / kChunk;
+        }
+    }
+    s.hcap = hcap;
+    s.tcap = tcap;
+    CKS(dalloc_t(g, &s.hentry, (size_t)hcap));
+    CKS(dalloc_t(g, &s.hacc, (size_t)hcap * kLanes * 2));
+    CKS(dalloc_t(g, &s.hcarry, (size_t)hcap));
+    CKS(dalloc_t(g, &s.tasks, (size_t)tcap));
+    CK(g, cudaMemset(s.hacc, 0, (size_t)hcap * kLanes * 2 * sizeof(u64)));
+    CK(g, cudaMemset(s.hcarry, 0, (size_t)hcap * sizeof(u64)));
     CKS(dalloc_t(g, &s.ctr, 1));
     CKS(dalloc_t(g, &s.d_src, kLanes));
     CK(g, cudaMallocHost((void**)&s.hctr, sizeof(Counters)));
     CK(g, cudaMemset(s.nx, 0, n * sizeof(u64)));
     g->slot_ready = true;
+    return GBBC_OK;
+}
+
+gbbc_status alloc_wide(gbbc_graph* g) {
+    Slot& s = g->slot;
+    if (s.sN) return GBBC_OK;
+    size_t n = (size_t)std::max<int32_t>(g->n, 1);
+    CKS(dalloc_t(g, &s.sN, n * kLanes));
+    CKS(dalloc_t(g, &s.sX, n * kLanes));
+    CKS(dalloc_t(g, &s.psi_e, n * kLanes));
     return GBBC_OK;
 }
 
@@ -335,7 +364,28 @@ gbbc_status resolve(gbbc_graph* g, std::vector<Timed>& pend) {
 
 inline double dmin(double a, double b) { return a < b ? a : b; }
 
+gbbc_status run_batch_once(gbbc_graph* g, const BatchDesc& b, cudaStream_t st, bool wide, bool* need_wide);
+
+// A batch runs in the narrow sigma format unless the handle has met a count
+// >= 2^64 before; if the narrow forward meets one, the batch is rerun in the
+// wide format (which keeps sigma mod 2^64 as well) and later batches start
+// wide.  The backward only runs once, on the final forward.
 gbbc_status run_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
+    bool wide = g->wide_sticky;
+    if (wide) CKS(alloc_wide(g));
+    bool need_wide = false;
+    CKS(run_batch_once(g, b, st, wide, &need_wide));
+    if (need_wide) {
+        CKS(alloc_wide(g));
+        g->wide_sticky = true;
+        CKS(run_batch_once(g, b, st, true, &need_wide));
+    }
+    if (g->wide_sticky) g->stats.wide_batches++;
+    return GBBC_OK;
+}
+
+gbbc_status run_batch_once(gbbc_graph* g, const BatchDesc& b, cudaStream_t st, bool wide, bool* need_wide) {
+    *need_wide = false;
     Slot& s = g->slot;
     Csr c{g->n, g->nnz, g->d_row_ptr, g->d_col};
     const int32_t lo = b.lo, hi = b.hi;
@@ -480,9 +530,9 @@ gbbc_status run_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
         lanes = s.hctr->lanes;
         CK(g, cudaMemsetAsync((char*)s.ctr + gath_off, 0, gath_bytes, st));
         CKS(mark(&e0));
-        launch_fwd_gather(c, s, q_hi, new_hi, level, hd, g->nsm, st);
+        launch_fwd_gather(c, s, q_hi, new_hi, level, hd, g->nsm, st, wide);
         CKS(mark(&e1));
-        g->stats.kernel_launches += 2;
+        g->stats.kernel_launches += wide ? 2 : 3;
         CK(g, cudaGetLastError());
         if (tr) {
             // sigma reads of level `level` + writes of level+1 (lane counts of
@@ -499,9 +549,12 @@ gbbc_status run_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
     CK(g, cudaMemcpyAsync(s.hctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CK(g, cudaStreamSynchronize(st));
     if (s.hctr->err) return fail(g, GBBC_ERR_CAPACITY, "row list overflow (flags %u)", s.hctr->err);
-    if (s.hctr->carry)
-        return fail(g, GBBC_ERR_CAPACITY,
-                    "a shortest-path count reached 2^64 and the wide sigma format is not available");
+    if (s.hctr->carry && !wide) {  // rerun this batch in the wide format
+        if (tr) CKS(resolve(g, pend));
+        *need_wide = true;
+        g->batch_counter--;
+        return GBBC_OK;
+    }
     if (tr)  // sigma writes of each gathered level
         for (int l = 1; l < nlev; ++l) g->prof[PK_GATHER].bytes += 8.0 * (double)nl[l];
     // ---- kept state for parity checks ----
@@ -514,14 +567,14 @@ gbbc_status run_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
     }
     // ---- backward phase: levels nlev-1 .. 1 ----
     for (int l = nlev - 1; l >= 1; --l) {
-        CK(g, cudaMemsetAsync(&s.ctr->heavy, 0, sizeof(unsigned long long), st));
+        CK(g, cudaMemsetAsync(&s.ctr->heavy, 0, 2 * sizeof(unsigned long long), st));  // heavy, tasks
         CKS(mark(&e0));
-        launch_bwd(c, s, g->d_bc, off[l], off[l + 1], l, hd, g->nsm, st);
+        launch_bwd(c, s, g->d_bc, off[l], off[l + 1], l, hd, g->nsm, st, wide);
         CKS(mark(&e1));
-        g->stats.kernel_launches += 2;
+        g->stats.kernel_launches += 3;
         if (tr) {
             double succ_lanes = (l + 1 < nlev) ? (double)nl[l + 1] : 0.0;
-            double bytes = 52.0 * (double)nv[l] + 4.0 * (double)ne[l] + 16.0 * dmin((double)ne[l], nr) +
+            double bytes = 68.0 * (double)nv[l] + 4.0 * (double)ne[l] + 16.0 * dmin((double)ne[l], nr) +
                            8.0 * succ_lanes + 16.0 * (double)nl[l];
             long long rec = (l - 1 < (int)trace_rec.size()) ? trace_rec[l - 1] : -1;
             pend.push_back({PK_BWD, e0, e1, rec, 3, bytes, true});
@@ -595,8 +648,10 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
 
 gbbc_status finish_create(gbbc_graph* g, cudaStream_t st) {
     bc_clear_trace(g);
-    CKS(dalloc_t(g, &g->d_bc, (size_t)std::max<int32_t>(g->n, 1)));
-    CK(g, cudaMemsetAsync(g->d_bc, 0, (size_t)std::max<int32_t>(g->n, 1) * sizeof(double), st));
+    size_t n1 = (size_t)std::max<int32_t>(g->n, 1);
+    CKS(dalloc_t(g, &g->d_bc, 2 * n1));
+    CKS(dalloc_t(g, &g->d_bc_out, n1));
+    CK(g, cudaMemsetAsync(g->d_bc, 0, 2 * n1 * sizeof(u64), st));
     g->stats.batch_width = g->opt.batch_width == 0 ? 64 : g->opt.batch_width;
     g->stats.policy = g->opt.policy;
     CK(g, cudaStreamSynchronize(st));
@@ -752,9 +807,15 @@ gbbc_status bc_read(gbbc_graph* g, double* bc_out, int32_t graph_id, void* strea
     long long lo = graph_id < 0 ? 0 : g->goff[graph_id];
     long long hi = graph_id < 0 ? g->n : g->goff[graph_id + 1];
     cudaStream_t st = (cudaStream_t)stream;
-    if (hi > lo)
-        CK(g, cudaMemcpyAsync(bc_out, g->d_bc + lo, (size_t)(hi - lo) * sizeof(double),
-                              is_device_ptr(bc_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (hi > lo) {
+        bool dev = is_device_ptr(bc_out);
+        double* dst = dev ? bc_out : g->d_bc_out;
+        launch_bc_to_double(g->d_bc + 2 * lo, dst, hi - lo, false, st);
+        g->stats.kernel_launches++;
+        CK(g, cudaGetLastError());
+        if (!dev)
+            CK(g, cudaMemcpyAsync(bc_out, dst, (size_t)(hi - lo) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     CK(g, cudaStreamSynchronize(st));
     return GBBC_OK;
 }
@@ -776,7 +837,7 @@ gbbc_status bc_read_source_state(gbbc_graph* g, int64_t source_index, int32_t* d
 gbbc_status bc_reset(gbbc_graph* g) {
     if (!g) return GBBC_ERR_INVALID;
     CK(g, cudaStreamSynchronize(g->last_stream));
-    CK(g, cudaMemset(g->d_bc, 0, (size_t)std::max<int32_t>(g->n, 1) * sizeof(double)));
+    CK(g, cudaMemset(g->d_bc, 0, 2 * (size_t)std::max<int32_t>(g->n, 1) * sizeof(u64)));
     CKS(alloc_keep(g, 0, nullptr));
     return GBBC_OK;
 }

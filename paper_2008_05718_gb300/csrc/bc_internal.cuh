@@ -11,9 +11,10 @@
 //              CSR order (integer adds mod 2^64 with carry detection).
 //   backward - levels in reverse; for each (v, lane) at level l, the
 //              successors are the neighbours at level l+1 in that lane, and
-//              delta_s(v) = sigma_v * sum_w (1 + delta_w) / sigma_w  (Eq. 2)
-//              summed in CSR order, written back as coef_v = (1+delta_v)/sigma_v.
-//              BC[v] += sum over lanes of delta (fixed-order tree reduction).
+//              delta_s(v) = sigma_v * sum_w (1 + delta_w) / sigma_w  (Eq. 2),
+//              accumulated in 128-bit fixed point (bc_fixed.cuh) and written
+//              back as psi_v = (1 + delta_v) / sigma_v; BC[v] += sum over
+//              lanes of delta, also in 128-bit fixed point (units 2^-64).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -26,6 +27,8 @@ constexpr int kLanes = 64;         // sources per batch word
 constexpr int kWarp = 32;
 constexpr int kBlock = 256;        // threads per block of the warp-per-row kernels
 constexpr int kHeavyBlock = 512;   // threads per block of the block-per-row kernels
+constexpr int kChunk = 1024;       // CSR entries per chunk task of a heavy row
+constexpr int kChunkBlock = 256;   // threads per block of the chunk-task kernels
 
 typedef unsigned long long u64;
 
@@ -44,7 +47,8 @@ struct __align__(16) Counters {
     unsigned long long qtail;     // next free position in the entry queue
     unsigned long long lane_sum;  // gather: sum of popc(mask) of its entries
     unsigned long long lane_esum; // gather: sum of popc(mask) * degree
-    unsigned long long heavy;     // rows deferred to the block-per-row kernel
+    unsigned long long heavy;     // heavy rows of this step (accumulator slots)
+    unsigned long long tasks;     // chunk tasks of the heavy rows
     unsigned long long medium;    // rows deferred to the warp-per-row pull kernel
     unsigned long long edge_sum;  // discovery: sum of degrees of new vertices
     unsigned long long scanned;   // discovery: CSR entries read by a pull step
@@ -61,10 +65,22 @@ struct Slot {
     u64* ovf = nullptr;      // [n] lanes whose sigma(v) >= 2^64
     MaskTag* F = nullptr;    // [2][n] frontier masks by level parity
     u64* sigma = nullptr;    // [n][64] sigma mod 2^64, lane-minor
-    double* coef = nullptr;  // [n][64] (1 + delta) / sigma, lane-minor
+    u64* psi = nullptr;      // [n][64] (1 + delta) / sigma as double bits, lane-minor
+    // wide sigma format (lanes whose sigma reached 2^64), allocated on demand
+    u64* sN = nullptr;       // [n][64] normalised 64-bit mantissa of sigma
+    int32_t* sX = nullptr;   // [n][64] exponent: sigma ~ sN * 2^sX
+    int32_t* psi_e = nullptr;// [n][64] exponent of psi (psi bits hold [1, 2))
     int32_t* qv = nullptr;   // [qcap] queued vertex per entry, levels back to back
     u64* qm = nullptr;       // [qcap] lanes of the entry
     int32_t* heavy = nullptr;// [n] deferred entries/rows of the current step
+    // heavy rows are split into chunk tasks of kChunk entries whose partial
+    // sums meet in per-row accumulators (exact integer atomics)
+    long long hcap = 0;      // heavy rows per step (vertices of degree > heavy_deg)
+    long long tcap = 0;      // chunk tasks per step
+    int32_t* hentry = nullptr; // [hcap] queue entry of heavy slot h
+    u64* hacc = nullptr;     // [hcap][64][2] per-lane accumulators (zero between steps)
+    u64* hcarry = nullptr;   // [hcap] lanes whose sigma sum carried
+    int2* tasks = nullptr;   // [tcap] (heavy slot, first CSR position)
     int32_t* medium = nullptr;// [n] rows deferred by the thread-per-row pull
     long long qcap = 0;
     Counters* ctr = nullptr; // device
@@ -86,9 +102,10 @@ void launch_push(const Csr& g, const Slot& s, long long q_lo, long long q_hi, in
 void launch_pull(const Csr& g, const Slot& s, int32_t lo, int32_t hi, u64 lanes, int level, int heavy_deg,
                  int nsm, cudaStream_t st);
 void launch_fwd_gather(const Csr& g, const Slot& s, long long q_lo, long long q_hi, int level, int heavy_deg,
-                       int nsm, cudaStream_t st);
-void launch_bwd(const Csr& g, const Slot& s, double* bc, long long q_lo, long long q_hi, int level,
-                int heavy_deg, int nsm, cudaStream_t st);
+                       int nsm, cudaStream_t st, bool wide);
+void launch_bwd(const Csr& g, const Slot& s, u64* bc_fixed, long long q_lo, long long q_hi, int level,
+                int heavy_deg, int nsm, cudaStream_t st, bool wide);
+void launch_bc_to_double(const u64* bc_fixed, double* out, long long n, bool add, cudaStream_t st);
 void launch_keep_dist(const Slot& s, long long q_lo, long long q_hi, int level, int32_t* dist, long long n_total,
                       long long first_src, int nsrc, cudaStream_t st);
 void launch_keep_sigma(const Slot& s, int32_t lo, int32_t hi, uint64_t* sigma, uint8_t* ovf, long long n_total,

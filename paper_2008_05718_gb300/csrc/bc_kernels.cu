@@ -3,13 +3,17 @@
 // Every kernel works on one batch slot (bc_internal.cuh).  Entries of the
 // frontier queue are (vertex, lane mask) pairs; the queue holds the levels
 // back to back, so the backward phase walks the same entries in reverse.
-// Rows are processed by a warp each; rows longer than `heavy_deg` are
-// deferred to a list that a second kernel processes with a whole block per
-// row.  All floating-point sums run in CSR order within a row, and across
-// warps of a block in warp order, so results do not depend on scheduling.
+// Rows are processed by a warp each.  Rows longer than `heavy_deg` are split
+// into chunk tasks of kChunk CSR entries that blocks on many SMs process in
+// parallel; their partial sums meet in a per-row accumulator through integer
+// atomics (exact and order-free), and a finish kernel completes the row.
+// Every sum is an integer sum, so results do not depend on scheduling.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
+
+#include "bc_fixed.cuh"
 #include "bc_internal.cuh"
 
 namespace gbbc {
@@ -57,31 +61,32 @@ static int grid_for(long long warps_needed, int nsm, int per_sm = 8) {
 
 // ---------------------------------------------------------------------------
 // Seed: lane j starts at source d_src[j]; sources repeated within a batch
-// share one queue entry.  One block of 64 threads.
+// share one queue entry (in order of first occurrence).  One block of 64.
 __global__ void k_seed(Slot s, int nsrc) {
     const int j = threadIdx.x;
     __shared__ int32_t src[kLanes];
+    __shared__ int first[kLanes];
     if (j < nsrc) src[j] = s.d_src[j];
+    __syncthreads();
+    u64 mask = 0;
+    bool fj = false;
+    if (j < nsrc) {
+        fj = true;
+        for (int i = 0; i < nsrc; ++i)
+            if (src[i] == src[j]) {
+                mask |= 1ull << i;
+                if (i < j) fj = false;
+            }
+        first[j] = fj ? 1 : 0;
+    }
     __syncthreads();
     if (j < nsrc) {
         int32_t v = src[j];
         atomicOr(&s.vis[v], 1ull << j);
         s.sigma[(size_t)v * kLanes + j] = 1ull;
-        bool first = true;
-        u64 mask = 0;
-        for (int i = 0; i < nsrc; ++i)
-            if (src[i] == v) {
-                mask |= 1ull << i;
-                if (i < j) first = false;
-            }
-        if (first) {
+        if (fj) {
             int pos = 0;  // distinct sources among lanes < j
-            for (int i = 0; i < j; ++i) {
-                bool fi = true;
-                for (int h = 0; h < i; ++h)
-                    if (src[h] == src[i]) { fi = false; break; }
-                pos += fi;
-            }
+            for (int i = 0; i < j; ++i) pos += first[i];
             s.qv[pos] = v;
             s.qm[pos] = mask;
             MaskTag t;
@@ -94,6 +99,57 @@ __global__ void k_seed(Slot s, int nsrc) {
 }
 
 void launch_seed(const Slot& s, int nsrc, cudaStream_t st) { k_seed<<<1, kLanes, 0, st>>>(s, nsrc); }
+
+// ---------------------------------------------------------------------------
+// Heavy rows: a warp that meets entry e with more than heavy_deg neighbours
+// reserves an accumulator slot h and ceil(deg / kChunk) chunk tasks.  All 32
+// threads of the warp call this.
+__device__ __forceinline__ void enqueue_heavy(const Slot& s, long long e, int32_t beg, int32_t end) {
+    const int lane = threadIdx.x & 31;
+    const int nch = (end - beg + kChunk - 1) / kChunk;
+    unsigned long long h = 0, t0 = 0;
+    if (lane == 0) {
+        h = atomicAdd(&s.ctr->heavy, 1ull);
+        t0 = atomicAdd(&s.ctr->tasks, (unsigned long long)nch);
+    }
+    h = __shfl_sync(FULL, h, 0);
+    t0 = __shfl_sync(FULL, t0, 0);
+    if ((long long)h >= s.hcap || (long long)(t0 + nch) > s.tcap) {
+        if (lane == 0) atomicOr(&s.ctr->err, 2u);
+        return;
+    }
+    if (lane == 0) s.hentry[h] = (int32_t)e;
+    for (int i = lane; i < nch; i += 32) s.tasks[t0 + i] = make_int2((int)h, beg + i * kChunk);
+}
+
+// Task t of this step, validated against the capacities (a task slot that
+// an overflowing reservation left unwritten is skipped).
+__device__ __forceinline__ bool load_task(const Slot& s, const Csr& g, long long t, int& h, long long& e,
+                                          int32_t& v, u64& m, int32_t& p0, int32_t& p1) {
+    int2 tk = s.tasks[t];
+    h = tk.x;
+    if (h < 0 || h >= s.hcap) return false;
+    e = s.hentry[h];
+    if (e < 0 || e >= s.qcap) return false;
+    v = s.qv[e];
+    if (v < 0 || v >= g.n) return false;
+    m = s.qm[e];
+    int32_t beg = g.row_ptr[v], end = g.row_ptr[v + 1];
+    p0 = tk.y;
+    if (p0 < beg || p0 >= end) return false;
+    p1 = p0 + kChunk < end ? p0 + kChunk : end;
+    return true;
+}
+
+__device__ __forceinline__ long long task_count(const Slot& s) {
+    long long c = (long long)s.ctr->tasks;
+    return c < s.tcap ? c : s.tcap;
+}
+
+__device__ __forceinline__ long long heavy_count(const Slot& s) {
+    long long c = (long long)s.ctr->heavy;
+    return c < s.hcap ? c : s.hcap;
+}
 
 // ---------------------------------------------------------------------------
 // Top-down discovery: for each frontier entry (v, m) and neighbour w, the
@@ -151,11 +207,7 @@ __global__ void k_push(Csr g, Slot s, long long q_lo, long long q_hi, int heavy_
         u64 m = s.qm[e];
         int32_t beg = __ldg(g.row_ptr + v), end = __ldg(g.row_ptr + v + 1);
         if (end - beg > heavy_deg) {
-            if (lane == 0) {
-                unsigned long long pos = atomicAdd(&s.ctr->heavy, 1ull);
-                if ((long long)pos < s.n) s.heavy[pos] = (int32_t)e;
-                else atomicOr(&s.ctr->err, 2u);
-            }
+            enqueue_heavy(s, e, beg, end);
             continue;
         }
         push_row(g, s, m, beg, end, lane, kWarp, stats);
@@ -163,14 +215,17 @@ __global__ void k_push(Csr g, Slot s, long long q_lo, long long q_hi, int heavy_
     flush_stats(s, stats);
 }
 
-__global__ void k_push_heavy(Csr g, Slot s) {
-    const long long cnt = (long long)s.ctr->heavy;
+// Chunk tasks of heavy frontier rows: a block per task.
+__global__ void k_push_tasks(Csr g, Slot s) {
+    const long long cnt = task_count(s);
     StepStats stats = {0ull, 0ull, 0ull};
-    for (long long h = blockIdx.x; h < cnt; h += gridDim.x) {
-        long long e = s.heavy[h];
-        int32_t v = s.qv[e];
-        u64 m = s.qm[e];
-        push_row(g, s, m, g.row_ptr[v], g.row_ptr[v + 1], threadIdx.x, blockDim.x, stats);
+    for (long long t = blockIdx.x; t < cnt; t += gridDim.x) {
+        int h;
+        long long e;
+        int32_t v, p0, p1;
+        u64 m;
+        if (!load_task(s, g, t, h, e, v, m, p0, p1)) continue;
+        push_row(g, s, m, p0, p1, threadIdx.x, blockDim.x, stats);
     }
     flush_stats(s, stats);
 }
@@ -181,7 +236,7 @@ void launch_push(const Csr& g, const Slot& s, long long q_lo, long long q_hi, in
     long long cnt = q_hi - q_lo;
     if (cnt <= 0) return;
     k_push<<<grid_for(cnt, nsm), kBlock, 0, st>>>(g, s, q_lo, q_hi, heavy_deg);
-    k_push_heavy<<<nsm * 2, kHeavyBlock, 0, st>>>(g, s);
+    k_push_tasks<<<nsm * 4, kChunkBlock, 0, st>>>(g, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -323,12 +378,87 @@ void launch_pull(const Csr& g, const Slot& s, int32_t lo, int32_t hi, u64 lanes,
 // j of the mask, sigma[w][j] = sum over neighbours v whose level-`level`
 // mask has bit j of sigma[v][j], in CSR order, mod 2^64; a carry marks the
 // lane in ovf[w].  Thread t owns lanes t and t+32.
+//
+// WIDE additionally keeps sigma of overflowed lanes as N * 2^X (N a
+// normalised 64-bit mantissa, X an int32 exponent): terms are aligned to the
+// largest exponent seen and summed in a u128, so the mantissa keeps 64 bits.
+struct WideAcc {
+    u128 a;   // sum, units of 2^x
+    int x;    // exponent of a's unit; INT_MIN while empty
+    bool ovf; // a predecessor overflowed
+};
+
+__device__ __forceinline__ u128 shr128(u128 a, int r) {
+    u128 t;
+    if (r <= 0) return a;
+    if (r >= 128) { t.lo = t.hi = 0ull; return t; }
+    if (r >= 64) { t.lo = a.hi >> (r - 64); t.hi = 0ull; return t; }
+    t.lo = (a.lo >> r) | (a.hi << (64 - r));
+    t.hi = a.hi >> r;
+    return t;
+}
+
+__device__ __forceinline__ void wide_add(WideAcc& w, u128 v, int x) {
+    if (v.lo == 0ull && v.hi == 0ull) return;
+    if (w.x == INT_MIN) { w.a = v; w.x = x; return; }
+    if (x > w.x) { w.a = shr128(w.a, x - w.x); w.x = x; }
+    else v = shr128(v, w.x - x);
+    w.a = add128(w.a, v);
+}
+
 struct GatherAcc {
     u64 a0, a1;
     unsigned c0, c1;
+    WideAcc w0, w1;
 };
 
-template <int NT>
+__device__ __forceinline__ void gather_init(GatherAcc& acc) {
+    acc.a0 = acc.a1 = 0ull;
+    acc.c0 = acc.c1 = 0u;
+    acc.w0.a.lo = acc.w0.a.hi = acc.w1.a.lo = acc.w1.a.hi = 0ull;
+    acc.w0.x = acc.w1.x = INT_MIN;
+    acc.w0.ovf = acc.w1.ovf = false;
+}
+
+// sigma of predecessor (v, lane) as mantissa/exponent
+template <bool WIDE>
+__device__ __forceinline__ void pred_term(const Slot& s, int32_t v, int lane_id, u64 x, u64 ovf_v, WideAcc& w) {
+    if (!WIDE) return;
+    u128 t;
+    int X;
+    if ((ovf_v >> lane_id) & 1ull) {
+        t.lo = s.sN[(size_t)v * kLanes + lane_id];
+        X = s.sX[(size_t)v * kLanes + lane_id];
+        w.ovf = true;
+    } else {
+        t.lo = x;  // exact: x * 2^0
+        X = 0;
+    }
+    t.hi = 0ull;
+    wide_add(w, t, X);
+}
+
+// Up to four contributing neighbours per round: their (vertex, mask) pairs
+// are broadcast from the ballot, then all loads are issued before any is
+// used, so a warp keeps several independent loads in flight.
+struct Round4 {
+    int32_t v[4];
+    u64 f[4];
+};
+
+__device__ __forceinline__ void take_round(unsigned& bal, int32_t v, u64 f, Round4& r) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int src = bal ? __ffs(bal) - 1 : -1;
+        if (bal) bal &= bal - 1;
+        int sl = src < 0 ? 0 : src;
+        r.v[u] = __shfl_sync(FULL, v, sl);
+        u64 ff = shfl64(f, sl);
+        r.f[u] = src < 0 ? 0ull : ff;
+    }
+}
+
+template <int NT, bool WIDE>
 __device__ __forceinline__ void fwd_gather_row(const Csr& g, const Slot& s, const MaskTag* F, int level, u64 m,
                                                int32_t beg, int32_t end, int first, GatherAcc& acc) {
     // this warp handles chunks starting at beg + first*32, stepping NT*32
@@ -343,39 +473,84 @@ __device__ __forceinline__ void fwd_gather_row(const Csr& g, const Slot& s, cons
             if (t.tag == level) f = t.mask & m;
         }
         unsigned bal = __ballot_sync(FULL, f != 0);
-        while (bal) {
-            int src = __ffs(bal) - 1;
-            bal &= bal - 1;
-            int32_t vv = __shfl_sync(FULL, v, src);
-            u64 ff = shfl64(f, src);
-            const u64* row = s.sigma + (size_t)vv * kLanes;
-            if ((ff >> lane) & 1ull) {
-                u64 x = __ldg(row + lane);
-                acc.a0 += x;
-                acc.c0 |= acc.a0 < x;
+        if (WIDE) {
+            while (bal) {
+                int src = __ffs(bal) - 1;
+                bal &= bal - 1;
+                int32_t vv = __shfl_sync(FULL, v, src);
+                u64 ff = shfl64(f, src);
+                const u64* row = s.sigma + (size_t)vv * kLanes;
+                u64 ov = s.ovf[vv];
+                if ((ff >> lane) & 1ull) {
+                    u64 x = __ldg(row + lane);
+                    acc.a0 += x;
+                    acc.c0 |= acc.a0 < x;
+                    pred_term<WIDE>(s, vv, lane, x, ov, acc.w0);
+                }
+                if ((ff >> (lane + 32)) & 1ull) {
+                    u64 x = __ldg(row + lane + 32);
+                    acc.a1 += x;
+                    acc.c1 |= acc.a1 < x;
+                    pred_term<WIDE>(s, vv, lane + 32, x, ov, acc.w1);
+                }
             }
-            if ((ff >> (lane + 32)) & 1ull) {
-                u64 x = __ldg(row + lane + 32);
-                acc.a1 += x;
-                acc.c1 |= acc.a1 < x;
+        } else {
+            while (bal) {
+                Round4 r;
+                take_round(bal, v, f, r);
+                u64 x0[4], x1[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const u64* row = s.sigma + (size_t)r.v[u] * kLanes;
+                    x0[u] = ((r.f[u] >> lane) & 1ull) ? __ldg(row + lane) : 0ull;
+                    x1[u] = ((r.f[u] >> (lane + 32)) & 1ull) ? __ldg(row + lane + 32) : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    acc.a0 += x0[u];
+                    acc.c0 |= acc.a0 < x0[u];
+                    acc.a1 += x1[u];
+                    acc.c1 |= acc.a1 < x1[u];
+                }
             }
         }
     }
 }
 
+template <bool WIDE>
+__device__ __forceinline__ void wide_store(const Slot& s, int32_t w, int lane_id, const WideAcc& a) {
+    // normalise to a 64-bit mantissa (truncating) and exponent
+    int lz = clz128(a.a);
+    int bits = 128 - lz;
+    u64 N;
+    if (bits > 64) N = shr128(a.a, bits - 64).lo;
+    else N = a.a.lo << (64 - bits);
+    s.sN[(size_t)w * kLanes + lane_id] = N;
+    s.sX[(size_t)w * kLanes + lane_id] = a.x + bits - 64;
+}
+
+template <bool WIDE>
 __device__ __forceinline__ void fwd_store(const Slot& s, int32_t w, u64 m, const GatherAcc& acc) {
     const int lane = threadIdx.x & 31;
     u64* row = s.sigma + (size_t)w * kLanes;
-    if ((m >> lane) & 1ull) row[lane] = acc.a0;
-    if ((m >> (lane + 32)) & 1ull) row[lane + 32] = acc.a1;
-    unsigned b0 = __ballot_sync(FULL, acc.c0 && ((m >> lane) & 1ull));
-    unsigned b1 = __ballot_sync(FULL, acc.c1 && ((m >> (lane + 32)) & 1ull));
+    const bool l0 = (m >> lane) & 1ull, l1 = (m >> (lane + 32)) & 1ull;
+    if (l0) row[lane] = acc.a0;
+    if (l1) row[lane + 32] = acc.a1;
+    bool o0 = l0 && (acc.c0 || (WIDE && acc.w0.ovf));
+    bool o1 = l1 && (acc.c1 || (WIDE && acc.w1.ovf));
+    if (WIDE) {
+        if (o0) wide_store<WIDE>(s, w, lane, acc.w0);
+        if (o1) wide_store<WIDE>(s, w, lane + 32, acc.w1);
+    }
+    unsigned b0 = __ballot_sync(FULL, o0);
+    unsigned b1 = __ballot_sync(FULL, o1);
     if (lane == 0 && (b0 | b1)) {
         s.ovf[w] |= ((u64)b1 << 32) | b0;
         atomicOr(&s.ctr->carry, 1u);
     }
 }
 
+template <bool WIDE>
 __global__ void k_fwd_gather(Csr g, Slot s, long long q_lo, long long q_hi, int level, int heavy_deg) {
     const int lane = threadIdx.x & 31;
     const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
@@ -400,16 +575,22 @@ __global__ void k_fwd_gather(Csr g, Slot s, long long q_lo, long long q_hi, int 
             lesum += (unsigned long long)pc * (unsigned long long)(end - beg);
         }
         if (end - beg > heavy_deg) {
-            if (lane == 0) {
-                unsigned long long pos = atomicAdd(&s.ctr->heavy, 1ull);
-                if ((long long)pos < s.n) s.heavy[pos] = (int32_t)e;
-                else atomicOr(&s.ctr->err, 2u);
+            if (WIDE) {  // block per row (the wide sum is not order-free)
+                if (lane == 0) {
+                    unsigned long long pos = atomicAdd(&s.ctr->heavy, 1ull);
+                    if ((long long)pos < s.n) s.heavy[pos] = (int32_t)e;
+                    else atomicOr(&s.ctr->err, 2u);
+                }
+            } else {
+                __syncwarp();
+                enqueue_heavy(s, e, beg, end);
             }
             continue;
         }
-        GatherAcc acc = {0ull, 0ull, 0u, 0u};
-        fwd_gather_row<1>(g, s, F, level, m, beg, end, 0, acc);
-        fwd_store(s, w, m, acc);
+        GatherAcc acc;
+        gather_init(acc);
+        fwd_gather_row<1, WIDE>(g, s, F, level, m, beg, end, 0, acc);
+        fwd_store<WIDE>(s, w, m, acc);
     }
     if (lane == 0 && lsum) {
         atomicAdd(&s.ctr->lane_sum, lsum);
@@ -417,61 +598,172 @@ __global__ void k_fwd_gather(Csr g, Slot s, long long q_lo, long long q_hi, int 
     }
 }
 
-// Block per heavy row: warps take interleaved 32-entry chunks; partial sums
-// are combined in warp order (integer sums: order-free; carries OR-ed, and
-// a carry in the combination counts too).
-__global__ void k_fwd_gather_heavy(Csr g, Slot s, int level) {
+// Wide format: block per heavy row; warp partial sums combined in warp order.
+__global__ void k_fwd_gather_heavy_wide(Csr g, Slot s, int level) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int NW = kHeavyBlock / kWarp;
     const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
     __shared__ u64 ps[NW][kLanes];
     __shared__ unsigned pc[NW][kLanes];
+    __shared__ WideAcc pw[NW][kLanes];
     const long long cnt = (long long)s.ctr->heavy;
     for (long long h = blockIdx.x; h < cnt; h += gridDim.x) {
         long long e = s.heavy[h];
         int32_t w = s.qv[e];
         u64 m = s.qm[e];
-        GatherAcc acc = {0ull, 0ull, 0u, 0u};
-        fwd_gather_row<NW>(g, s, F, level, m, g.row_ptr[w], g.row_ptr[w + 1], wid, acc);
+        GatherAcc acc;
+        gather_init(acc);
+        fwd_gather_row<NW, true>(g, s, F, level, m, g.row_ptr[w], g.row_ptr[w + 1], wid, acc);
         ps[wid][lane] = acc.a0;
         ps[wid][lane + 32] = acc.a1;
         pc[wid][lane] = acc.c0;
         pc[wid][lane + 32] = acc.c1;
+        pw[wid][lane] = acc.w0;
+        pw[wid][lane + 32] = acc.w1;
         __syncthreads();
         if (wid == 0) {
-            GatherAcc tot = {0ull, 0ull, 0u, 0u};
+            GatherAcc tot;
+            gather_init(tot);
             for (int i = 0; i < NW; ++i) {
                 u64 x0 = ps[i][lane], x1 = ps[i][lane + 32];
                 tot.a0 += x0;
                 tot.c0 |= (tot.a0 < x0) | pc[i][lane];
                 tot.a1 += x1;
                 tot.c1 |= (tot.a1 < x1) | pc[i][lane + 32];
+                WideAcc q0 = pw[i][lane], q1 = pw[i][lane + 32];
+                if (q0.x != INT_MIN) wide_add(tot.w0, q0.a, q0.x);
+                if (q1.x != INT_MIN) wide_add(tot.w1, q1.a, q1.x);
+                tot.w0.ovf |= q0.ovf;
+                tot.w1.ovf |= q1.ovf;
             }
-            fwd_store(s, w, m, tot);
+            fwd_store<true>(s, w, m, tot);
         }
         __syncthreads();
     }
 }
 
+// Narrow format: chunk tasks of heavy rows (block of 8 warps per task) add
+// their per-lane partial sums into hacc[h][lane] with 64-bit atomics; a
+// carry of any add (or inside a partial) marks the lane in hcarry[h].
+__global__ void k_fwd_gather_tasks(Csr g, Slot s, int level) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int NW = kChunkBlock / kWarp;
+    const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
+    __shared__ u64 ps[NW][kLanes];
+    __shared__ unsigned pc[NW][kLanes];
+    const long long cnt = task_count(s);
+    for (long long t = blockIdx.x; t < cnt; t += gridDim.x) {
+        int h;
+        long long e;
+        int32_t v, p0, p1;
+        u64 m;
+        bool ok = load_task(s, g, t, h, e, v, m, p0, p1);
+        GatherAcc acc;
+        gather_init(acc);
+        if (ok) fwd_gather_row<NW, false>(g, s, F, level, m, p0, p1, wid, acc);
+        ps[wid][lane] = acc.a0;
+        ps[wid][lane + 32] = acc.a1;
+        pc[wid][lane] = acc.c0;
+        pc[wid][lane + 32] = acc.c1;
+        __syncthreads();
+        if (wid == 0 && ok) {
+            u64 carry = 0;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                int j = lane + 32 * half;
+                u64 sum = 0;
+                unsigned c = 0;
+                for (int i = 0; i < NW; ++i) {
+                    u64 x = ps[i][j];
+                    sum += x;
+                    c |= (sum < x) | pc[i][j];
+                }
+                if ((m >> j) & 1ull) {
+                    u64 old = atomicAdd(s.hacc + ((size_t)h * kLanes + j) * 2, sum);
+                    c |= (old + sum) < old;
+                    if (c) carry |= 1ull << j;
+                }
+            }
+            u64 cw = warp_or64(carry);
+            if (lane == 0 && cw) atomicOr(s.hcarry + h, cw);
+        }
+        __syncthreads();
+    }
+}
+
+// Finish the heavy rows: warp per row reads and clears its accumulators.
+__global__ void k_fwd_gather_finish(Slot s) {
+    const int lane = threadIdx.x & 31;
+    const long long cnt = heavy_count(s);
+    for (long long h = gwarp(); h < cnt; h += nwarps()) {
+        long long e = s.hentry[h];
+        int32_t w = s.qv[e];
+        u64 m = s.qm[e];
+        u64* a = s.hacc + (size_t)h * kLanes * 2;
+        GatherAcc acc;
+        gather_init(acc);
+        u64 cw = s.hcarry[h];
+        acc.a0 = a[2 * lane];
+        acc.a1 = a[2 * (lane + 32)];
+        acc.c0 = (unsigned)((cw >> lane) & 1ull);
+        acc.c1 = (unsigned)((cw >> (lane + 32)) & 1ull);
+        a[2 * lane] = 0ull;
+        a[2 * (lane + 32)] = 0ull;
+        __syncwarp();
+        if (lane == 0) s.hcarry[h] = 0ull;
+        fwd_store<false>(s, w, m, acc);
+    }
+}
+
 void launch_fwd_gather(const Csr& g, const Slot& s, long long q_lo, long long q_hi, int level, int heavy_deg,
-                       int nsm, cudaStream_t st) {
+                       int nsm, cudaStream_t st, bool wide) {
     long long cnt = q_hi - q_lo;
     if (cnt <= 0) return;
-    k_fwd_gather<<<grid_for(cnt, nsm), kBlock, 0, st>>>(g, s, q_lo, q_hi, level, heavy_deg);
-    k_fwd_gather_heavy<<<nsm * 2, kHeavyBlock, 0, st>>>(g, s, level);
+    if (wide) {
+        k_fwd_gather<true><<<grid_for(cnt, nsm), kBlock, 0, st>>>(g, s, q_lo, q_hi, level, heavy_deg);
+        k_fwd_gather_heavy_wide<<<nsm * 2, kHeavyBlock, 0, st>>>(g, s, level);
+    } else {
+        k_fwd_gather<false><<<grid_for(cnt, nsm), kBlock, 0, st>>>(g, s, q_lo, q_hi, level, heavy_deg);
+        k_fwd_gather_tasks<<<nsm * 4, kChunkBlock, 0, st>>>(g, s, level);
+        k_fwd_gather_finish<<<nsm, kBlock, 0, st>>>(s);
+    }
 }
 
 // ---------------------------------------------------------------------------
-// Backward step for the entries of level `level` (>= 1): successors of
-// (v, lane j) are the neighbours w whose level-(level+1) mask has bit j.
-//   acc_j   = sum over successors of coef[w][j]          (CSR order, FP64)
-//   delta_j = sigma_v * acc_j                              (Eq. 2)
-//   coef[v][j] = 1/sigma_v + acc_j  = (1 + delta_j) / sigma_v
-//   BC[v]  += sum over lanes of delta_j                    (fixed tree order)
+// Backward step for the entries of level `level` (>= 1), in the integer
+// fixed-point form of bc_fixed.cuh.  Successors of (v, lane j) are the
+// neighbours w whose level-(level+1) mask has bit j.  Per (v, j):
+//   A     = sum over successors of psi_w * 2^(E_v + 64)       (u128)
+//   delta = N_v * A / 2^63                                    (units 2^-64)
+//   psi_v = (floor(2^127 / N_v) + A) * 2^(-64 - E_v)         (stored rounded)
+//   BC[v] += sum over lanes of delta                          (u128)
 // The entry's own mask is published with tag `level` for the next step.
-template <int NT>
+
+// sigma of (v, lane) as normalised mantissa N and exponent E = floor(log2)
+template <bool WIDE>
+__device__ __forceinline__ void sigma_norm(const Slot& s, int32_t v, int lane_id, u64 ovf_v, u64& N, int& E) {
+    if (WIDE && ((ovf_v >> lane_id) & 1ull)) {
+        N = s.sN[(size_t)v * kLanes + lane_id];
+        E = s.sX[(size_t)v * kLanes + lane_id] + 63;
+    } else {
+        u64 x = s.sigma[(size_t)v * kLanes + lane_id];
+        int lz = __clzll(x);
+        N = x << lz;
+        E = 63 - lz;
+    }
+}
+
+template <bool WIDE>
+__device__ __forceinline__ u128 psi_term(u64 bits, int eoff, int Ev) {
+    int e = (int)((bits >> 52) & 0x7FFull) - 1023 + (WIDE ? eoff : 0);
+    u64 M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    return shl_term(M, e + Ev + 12);
+}
+
+template <int NT, bool WIDE>
 __device__ __forceinline__ void bwd_gather_row(const Csr& g, const Slot& s, const MaskTag* Fs, int level, u64 m,
-                                               int32_t beg, int32_t end, int first, double& a0, double& a1) {
+                                               int32_t beg, int32_t end, int first, int E0, int E1, u128& a0,
+                                               u128& a1) {
     const int lane = threadIdx.x & 31;
     for (int32_t base = beg + first * kWarp; base < end; base += NT * kWarp) {
         int32_t p = base + lane;
@@ -484,39 +776,85 @@ __device__ __forceinline__ void bwd_gather_row(const Csr& g, const Slot& s, cons
         }
         unsigned bal = __ballot_sync(FULL, f != 0);
         while (bal) {
-            int src = __ffs(bal) - 1;
-            bal &= bal - 1;
-            int32_t ww = __shfl_sync(FULL, w, src);
-            u64 ff = shfl64(f, src);
-            const double* row = s.coef + (size_t)ww * kLanes;
-            if ((ff >> lane) & 1ull) a0 += __ldg(row + lane);
-            if ((ff >> (lane + 32)) & 1ull) a1 += __ldg(row + lane + 32);
+            Round4 r;
+            take_round(bal, w, f, r);
+            u64 b0[4], b1[4];
+            int x0[4], x1[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                size_t at = (size_t)r.v[u] * kLanes;
+                bool q0 = (r.f[u] >> lane) & 1ull, q1 = (r.f[u] >> (lane + 32)) & 1ull;
+                b0[u] = q0 ? __ldg(s.psi + at + lane) : 0ull;
+                b1[u] = q1 ? __ldg(s.psi + at + lane + 32) : 0ull;
+                x0[u] = (WIDE && q0) ? __ldg(s.psi_e + at + lane) : 0;
+                x1[u] = (WIDE && q1) ? __ldg(s.psi_e + at + lane + 32) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if ((r.f[u] >> lane) & 1ull) a0 = add128(a0, psi_term<WIDE>(b0[u], x0[u], E0));
+                if ((r.f[u] >> (lane + 32)) & 1ull) a1 = add128(a1, psi_term<WIDE>(b1[u], x1[u], E1));
+            }
         }
     }
 }
 
-__device__ __forceinline__ void bwd_store(const Slot& s, double* bc, int32_t v, u64 m, double a0, double a1) {
-    const int lane = threadIdx.x & 31;
-    const u64* srow = s.sigma + (size_t)v * kLanes;
-    double* crow = s.coef + (size_t)v * kLanes;
-    double d0 = 0.0, d1 = 0.0;
-    if ((m >> lane) & 1ull) {
-        double sg = (double)srow[lane];
-        d0 = sg * a0;
-        crow[lane] = 1.0 / sg + a0;
+// per-lane finish: delta (returned, units 2^-64) and psi_v (stored)
+template <bool WIDE>
+__device__ __forceinline__ u128 bwd_lane(const Slot& s, int32_t v, int lane_id, u64 N, int E, u128 A) {
+    u128 d = mul_shift63(N, A);
+    u128 psi = add128(recip127(N), A);
+    u64 M;
+    int e;
+    round128(psi, -64 - E, M, e);
+    size_t at = (size_t)v * kLanes + lane_id;
+    if (WIDE) {
+        s.psi[at] = unit_bits(M);
+        s.psi_e[at] = e;
+    } else {
+        s.psi[at] = double_bits(M, e);
     }
-    if ((m >> (lane + 32)) & 1ull) {
-        double sg = (double)srow[lane + 32];
-        d1 = sg * a1;
-        crow[lane + 32] = 1.0 / sg + a1;
-    }
-    double c = d0 + d1;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
-    if (lane == 0) bc[v] += c;
+    return d;
 }
 
-__global__ void k_bwd(Csr g, Slot s, double* bc, long long q_lo, long long q_hi, int level, int heavy_deg) {
+__device__ __forceinline__ u128 shfl_xor128(u128 a, int o) {
+    u128 r;
+    r.lo = __shfl_xor_sync(FULL, a.lo, o);
+    r.hi = __shfl_xor_sync(FULL, a.hi, o);
+    return r;
+}
+
+template <bool WIDE>
+__device__ __forceinline__ void bwd_store(const Slot& s, u64* bc, int32_t v, u64 m, int E0, int E1, u64 N0, u64 N1,
+                                          u128 a0, u128 a1) {
+    const int lane = threadIdx.x & 31;
+    u128 c;
+    c.lo = c.hi = 0ull;
+    if ((m >> lane) & 1ull) c = add128(c, bwd_lane<WIDE>(s, v, lane, N0, E0, a0));
+    if ((m >> (lane + 32)) & 1ull) c = add128(c, bwd_lane<WIDE>(s, v, lane + 32, N1, E1, a1));
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) c = add128(c, shfl_xor128(c, o));
+    if (lane == 0) {
+        u128 b;
+        b.lo = bc[2 * (size_t)v];
+        b.hi = bc[2 * (size_t)v + 1];
+        b = add128(b, c);
+        bc[2 * (size_t)v] = b.lo;
+        bc[2 * (size_t)v + 1] = b.hi;
+    }
+}
+
+template <bool WIDE>
+__device__ __forceinline__ void lane_norms(const Slot& s, int32_t v, u64 m, u64& N0, int& E0, u64& N1, int& E1) {
+    const int lane = threadIdx.x & 31;
+    u64 ov = WIDE ? s.ovf[v] : 0ull;
+    N0 = N1 = 1ull << 63;
+    E0 = E1 = 0;
+    if ((m >> lane) & 1ull) sigma_norm<WIDE>(s, v, lane, ov, N0, E0);
+    if ((m >> (lane + 32)) & 1ull) sigma_norm<WIDE>(s, v, lane + 32, ov, N1, E1);
+}
+
+template <bool WIDE>
+__global__ void k_bwd(Csr g, Slot s, u64* bc, long long q_lo, long long q_hi, int level, int heavy_deg) {
     const int lane = threadIdx.x & 31;
     const MaskTag* Fs = s.F + (size_t)((level + 1) & 1) * s.n;
     MaskTag* Fo = s.F + (size_t)(level & 1) * s.n;
@@ -532,52 +870,117 @@ __global__ void k_bwd(Csr g, Slot s, double* bc, long long q_lo, long long q_hi,
             Fo[v] = t;
         }
         if (end - beg > heavy_deg) {
-            if (lane == 0) {
-                unsigned long long pos = atomicAdd(&s.ctr->heavy, 1ull);
-                if ((long long)pos < s.n) s.heavy[pos] = (int32_t)e;
-                else atomicOr(&s.ctr->err, 2u);
-            }
+            enqueue_heavy(s, e, beg, end);
             continue;
         }
-        double a0 = 0.0, a1 = 0.0;
-        bwd_gather_row<1>(g, s, Fs, level, m, beg, end, 0, a0, a1);
-        bwd_store(s, bc, v, m, a0, a1);
+        u64 N0, N1;
+        int E0, E1;
+        lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
+        u128 a0 = {0ull, 0ull}, a1 = {0ull, 0ull};
+        bwd_gather_row<1, WIDE>(g, s, Fs, level, m, beg, end, 0, E0, E1, a0, a1);
+        bwd_store<WIDE>(s, bc, v, m, E0, E1, N0, N1, a0, a1);
     }
 }
 
-__global__ void k_bwd_heavy(Csr g, Slot s, double* bc, int level) {
+// Chunk tasks of heavy rows: per-lane u128 partial sums are added into
+// hacc[h][lane] with two 64-bit atomics (the low word's carry goes into the
+// high word), which keeps the total exact whatever the order.
+__device__ __forceinline__ void atomic_add128(u64* a, u128 t) {
+    if ((t.lo | t.hi) == 0ull) return;
+    u64 old = atomicAdd(a, t.lo);
+    u64 carry = (old + t.lo) < old ? 1ull : 0ull;
+    if (t.hi + carry) atomicAdd(a + 1, t.hi + carry);
+}
+
+template <bool WIDE>
+__global__ void k_bwd_tasks(Csr g, Slot s, int level) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int NW = kHeavyBlock / kWarp;
+    constexpr int NW = kChunkBlock / kWarp;
     const MaskTag* Fs = s.F + (size_t)((level + 1) & 1) * s.n;
-    __shared__ double ps[NW][kLanes];
-    const long long cnt = (long long)s.ctr->heavy;
-    for (long long h = blockIdx.x; h < cnt; h += gridDim.x) {
-        long long e = s.heavy[h];
-        int32_t v = s.qv[e];
-        u64 m = s.qm[e];
-        double a0 = 0.0, a1 = 0.0;
-        bwd_gather_row<NW>(g, s, Fs, level, m, g.row_ptr[v], g.row_ptr[v + 1], wid, a0, a1);
+    __shared__ u128 ps[NW][kLanes];
+    const long long cnt = task_count(s);
+    for (long long t = blockIdx.x; t < cnt; t += gridDim.x) {
+        int h;
+        long long e;
+        int32_t v, p0, p1;
+        u64 m;
+        bool ok = load_task(s, g, t, h, e, v, m, p0, p1);
+        u128 a0 = {0ull, 0ull}, a1 = {0ull, 0ull};
+        if (ok) {
+            u64 N0, N1;
+            int E0, E1;
+            lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
+            bwd_gather_row<NW, WIDE>(g, s, Fs, level, m, p0, p1, wid, E0, E1, a0, a1);
+        }
         ps[wid][lane] = a0;
         ps[wid][lane + 32] = a1;
         __syncthreads();
-        if (wid == 0) {
-            double t0 = 0.0, t1 = 0.0;
+        if (wid == 0 && ok) {
+            u128 t0 = {0ull, 0ull}, t1 = {0ull, 0ull};
             for (int i = 0; i < NW; ++i) {
-                t0 += ps[i][lane];
-                t1 += ps[i][lane + 32];
+                t0 = add128(t0, ps[i][lane]);
+                t1 = add128(t1, ps[i][lane + 32]);
             }
-            bwd_store(s, bc, v, m, t0, t1);
+            u64* a = s.hacc + (size_t)h * kLanes * 2;
+            atomic_add128(a + 2 * lane, t0);
+            atomic_add128(a + 2 * (lane + 32), t1);
         }
         __syncthreads();
     }
 }
 
-void launch_bwd(const Csr& g, const Slot& s, double* bc, long long q_lo, long long q_hi, int level, int heavy_deg,
-                int nsm, cudaStream_t st) {
+template <bool WIDE>
+__global__ void k_bwd_finish(Slot s, u64* bc) {
+    const int lane = threadIdx.x & 31;
+    const long long cnt = heavy_count(s);
+    for (long long h = gwarp(); h < cnt; h += nwarps()) {
+        long long e = s.hentry[h];
+        int32_t v = s.qv[e];
+        u64 m = s.qm[e];
+        u64* a = s.hacc + (size_t)h * kLanes * 2;
+        u128 a0 = {a[2 * lane], a[2 * lane + 1]};
+        u128 a1 = {a[2 * (lane + 32)], a[2 * (lane + 32) + 1]};
+        a[2 * lane] = a[2 * lane + 1] = 0ull;
+        a[2 * (lane + 32)] = a[2 * (lane + 32) + 1] = 0ull;
+        u64 N0, N1;
+        int E0, E1;
+        lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
+        bwd_store<WIDE>(s, bc, v, m, E0, E1, N0, N1, a0, a1);
+    }
+}
+
+void launch_bwd(const Csr& g, const Slot& s, u64* bc, long long q_lo, long long q_hi, int level, int heavy_deg,
+                int nsm, cudaStream_t st, bool wide) {
     long long cnt = q_hi - q_lo;
     if (cnt <= 0) return;
-    k_bwd<<<grid_for(cnt, nsm), kBlock, 0, st>>>(g, s, bc, q_lo, q_hi, level, heavy_deg);
-    k_bwd_heavy<<<nsm * 2, kHeavyBlock, 0, st>>>(g, s, bc, level);
+    if (wide) {
+        k_bwd<true><<<grid_for(cnt, nsm), kBlock, 0, st>>>(g, s, bc, q_lo, q_hi, level, heavy_deg);
+        k_bwd_tasks<true><<<nsm * 4, kChunkBlock, 0, st>>>(g, s, level);
+        k_bwd_finish<true><<<nsm, kBlock, 0, st>>>(s, bc);
+    } else {
+        k_bwd<false><<<grid_for(cnt, nsm), kBlock, 0, st>>>(g, s, bc, q_lo, q_hi, level, heavy_deg);
+        k_bwd_tasks<false><<<nsm * 4, kChunkBlock, 0, st>>>(g, s, level);
+        k_bwd_finish<false><<<nsm, kBlock, 0, st>>>(s, bc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-point BC (u128, units 2^-64) to double, correctly rounded; with
+// add != 0 the value is added to out (the no-allocation entry point).
+__global__ void k_bc_to_double(const u64* bc, double* out, long long n, int add) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        u128 a;
+        a.lo = bc[2 * i];
+        a.hi = bc[2 * i + 1];
+        double d = fixed_to_double(a);
+        out[i] = add ? out[i] + d : d;
+    }
+}
+
+void launch_bc_to_double(const u64* bc, double* out, long long n, bool add, cudaStream_t st) {
+    if (n <= 0) return;
+    k_bc_to_double<<<1216, 256, 0, st>>>(bc, out, n, add ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------

@@ -19,7 +19,8 @@
 // any stream capture begins.
 //
 // The kernels are the same ones bc_compute launches (64 sources per batch);
-// this path always expands top-down and adds into the caller's BC vector.
+// this path always expands top-down, keeps this call's BC in the scratch's
+// 128-bit fixed-point vector and adds it into the caller's BC vector.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -42,14 +43,21 @@ constexpr long long kOffNx = kOffVis + align256(8 * kNoallocMaxVertices);
 constexpr long long kOffOvf = kOffNx + align256(8 * kNoallocMaxVertices);
 constexpr long long kOffF = kOffOvf + align256(8 * kNoallocMaxVertices);
 constexpr long long kOffSigma = kOffF + align256(2 * (long long)sizeof(MaskTag) * kNoallocMaxVertices);
-constexpr long long kOffCoef = kOffSigma + align256(8 * kLanes * kNoallocMaxVertices);
-constexpr long long kOffQv = kOffCoef + align256(8 * kLanes * kNoallocMaxVertices);
+constexpr long long kOffPsi = kOffSigma + align256(8 * kLanes * kNoallocMaxVertices);
+constexpr long long kOffBc = kOffPsi + align256(8 * kLanes * kNoallocMaxVertices);
+constexpr long long kOffQv = kOffBc + align256(16 * kNoallocMaxVertices);
 constexpr long long kOffQm = kOffQv + align256(4 * kNoallocQcap);
 constexpr long long kOffHeavy = kOffQm + align256(8 * kNoallocQcap);
 constexpr long long kOffMedium = kOffHeavy + align256(4 * kNoallocMaxVertices);
-constexpr long long kOffCtr = kOffMedium + align256(4 * kNoallocMaxVertices);
+constexpr long long kNoallocTcap = kNoallocMaxVertices * kNoallocMaxVertices / kChunk + kNoallocMaxVertices;
+constexpr long long kOffHentry = kOffMedium + align256(4 * kNoallocMaxVertices);
+constexpr long long kOffHacc = kOffHentry + align256(4 * kNoallocMaxVertices);
+constexpr long long kOffHcarry = kOffHacc + align256(16 * kLanes * kNoallocMaxVertices);
+constexpr long long kOffTasks = kOffHcarry + align256(8 * kNoallocMaxVertices);
+constexpr long long kOffCtr = kOffTasks + align256(8 * kNoallocTcap);
 constexpr long long kOffSrc = kOffCtr + align256((long long)sizeof(Counters));
 constexpr long long kScratchBytes = kOffSrc + align256(4 * kLanes);
+static_assert(kScratchBytes < (64ll << 20), "no-allocation scratch above 64 MiB");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -115,11 +123,18 @@ extern "C" gbbc_status bc_compute_noalloc(int32_t n, int64_t nnz, const int32_t*
     s.ovf = (u64*)(base + kOffOvf);
     s.F = (MaskTag*)(base + kOffF);
     s.sigma = (u64*)(base + kOffSigma);
-    s.coef = (double*)(base + kOffCoef);
+    s.psi = (u64*)(base + kOffPsi);
+    u64* bc_fixed = (u64*)(base + kOffBc);  // this call's BC, 128-bit fixed point
     s.qv = (int32_t*)(base + kOffQv);
     s.qm = (u64*)(base + kOffQm);
     s.heavy = (int32_t*)(base + kOffHeavy);
     s.medium = (int32_t*)(base + kOffMedium);
+    s.hentry = (int32_t*)(base + kOffHentry);
+    s.hacc = (u64*)(base + kOffHacc);
+    s.hcarry = (u64*)(base + kOffHcarry);
+    s.tasks = (int2*)(base + kOffTasks);
+    s.hcap = kNoallocMaxVertices;     // a row is heavy at most once per step
+    s.tcap = kNoallocTcap;            // nnz <= n^2 entries in chunks, plus one partial chunk per row
     s.ctr = (Counters*)(base + kOffCtr);
     s.d_src = (int32_t*)(base + kOffSrc);
     s.qcap = (long long)n * kLanes + kLanes;
@@ -130,6 +145,11 @@ extern "C" gbbc_status bc_compute_noalloc(int32_t n, int64_t nnz, const int32_t*
     const size_t disc_off = offsetof(Counters, heavy), disc_bytes = offsetof(Counters, err) - disc_off;
     const size_t gath_off = offsetof(Counters, lane_sum), gath_bytes = offsetof(Counters, medium) - gath_off;
 
+    NA_CK(cudaMemsetAsync(bc_fixed, 0, 2 * (size_t)n * sizeof(u64), st));
+    // heavy-row accumulators must start at zero (they are left at zero by
+    // every completed step, but the array may hold an aborted call's state)
+    NA_CK(cudaMemsetAsync(s.hacc, 0, (size_t)n * kLanes * 2 * sizeof(u64), st));
+    NA_CK(cudaMemsetAsync(s.hcarry, 0, (size_t)n * sizeof(u64), st));
     for (int64_t b0 = 0; b0 < k; b0 += kLanes) {
         const int nsrc = (int)((k - b0) < kLanes ? (k - b0) : kLanes);
         const int32_t* bsrc = sources + b0;
@@ -169,7 +189,7 @@ extern "C" gbbc_status bc_compute_noalloc(int32_t n, int64_t nnz, const int32_t*
             if (level + 2 > kNoallocMaxVertices + 1) return GBBC_ERR_CAPACITY;
             off[level + 2] = new_hi;
             NA_CK(cudaMemsetAsync((char*)s.ctr + gath_off, 0, gath_bytes, st));
-            launch_fwd_gather(c, s, q_hi, new_hi, level, heavy_deg, nsm, st);
+            launch_fwd_gather(c, s, q_hi, new_hi, level, heavy_deg, nsm, st, false);
             NA_CK(cudaGetLastError());
             ++level;
         }
@@ -178,11 +198,13 @@ extern "C" gbbc_status bc_compute_noalloc(int32_t n, int64_t nnz, const int32_t*
         NA_CK(cudaStreamSynchronize(st));
         if (hc.err || hc.carry) return GBBC_ERR_CAPACITY;
         for (int l = nlev - 1; l >= 1; --l) {
-            NA_CK(cudaMemsetAsync(&s.ctr->heavy, 0, sizeof(unsigned long long), st));
-            launch_bwd(c, s, bc_out, off[l], off[l + 1], l, heavy_deg, nsm, st);
+            NA_CK(cudaMemsetAsync(&s.ctr->heavy, 0, 2 * sizeof(unsigned long long), st));  // heavy, tasks
+            launch_bwd(c, s, bc_fixed, off[l], off[l + 1], l, heavy_deg, nsm, st, false);
         }
         NA_CK(cudaGetLastError());
     }
+    launch_bc_to_double(bc_fixed, bc_out, n, true, st);
+    NA_CK(cudaGetLastError());
     NA_CK(cudaStreamSynchronize(st));
     return GBBC_OK;
 }

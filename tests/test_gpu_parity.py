@@ -221,3 +221,49 @@ def bc_levels(ost, S, g):
         _, st = oracle.bc_graph(g, S[b:b + 64], dump=range(len(S[b:b + 64])))
         depths.append(max(int(st[i].dist.max()) for i in st))
     return sum(d + 1 for d in depths)
+
+
+# ---- the wide sigma format (counts >= 2^64) ---------------------------------
+
+@pytest.mark.parametrize("k", [63, 64, 65, 100])
+def test_wide_sigma_diamond_chain(gb, k):
+    g = gg.diamond_chain(k)
+    S = np.arange(g.n, dtype=np.int32)
+    got, stats = check(gb, g, S, keep=(0, g.n - 1, 3 * (k // 2)))
+    assert (stats["wide_batches"] > 0) == (k >= 64)
+    # every sigma in a diamond chain is a power of two: BC is exact
+    from test_oracle_pins import diamond_closed_form
+    assert np.array_equal(got, diamond_closed_form(k))
+
+
+def test_wide_sigma_full_grid(gb):
+    g = gg.full_grid(40, 40)  # sigma up to C(78, 39) ~ 2^75
+    S = np.arange(g.n, dtype=np.int32)
+    _, stats = check(gb, g, S, keep=(0, 39, 820, 1599))
+    assert stats["wide_batches"] > 0
+
+
+@pytest.mark.parametrize("policy", ["push", "auto"])
+def test_wide_sigma_grid_with_removed_edges(gb, policy):
+    g = gg.grid(96, "0.05", seed=17)
+    S = gg.sample_sources(g.n, 130, seed=17)
+    check(gb, g, S, keep=(0, 64, 129), policy=policy)
+
+
+def test_grid1024_full_size_sampled(gb):
+    # the high-diameter workload at full size: one batch of 64 sources;
+    # sigma exceeds the double range (~2^2000), dist/sigma mod 2^64 exact
+    g, S = gg.workload("grid1024")
+    got, stats = check(gb, g, S[:64], keep=(0, 63), batch_width=64)
+    assert stats["wide_batches"] == 1 and stats["levels_fwd"] > 1500
+
+
+def test_bc_bit_identical_across_schedules(gb):
+    # integer fixed-point accumulation: the schedule cannot change a bit
+    g = gg.rmat(12, 16, seed=19)
+    S = gg.sample_sources(g.n, 300, seed=19)
+    runs = [run_gpu(gb, g, S, policy=p, heavy_degree=h)[0]
+            for p, h in [("push", 0), ("pull", 0), ("beamer", 32), ("auto", 64)]]
+    runs.append(run_gpu(gb, g, S[::-1].copy())[0])  # other batch composition
+    for r in runs[1:]:
+        assert np.array_equal(r, runs[0])
