@@ -458,11 +458,8 @@ gbbc_status run_batch_once(gbbc_graph* g, const BatchDesc& b, cudaStream_t st, b
             r.nnz_range = nnz_range;
             r.frontier_vertices = nv[level];
             r.frontier_edges = ne[level];
-            r.frontier_lanes = nl[level];
-            long long vl = 0, vle = 0;
-            for (int i = 0; i <= level; ++i) { vl += nl[i]; vle += nle[i]; }
-            r.visited_lanes = vl;
-            r.visited_lane_edges = vle;
+            // lane counts of this level arrive with this step's read-back
+            r.frontier_lanes = r.visited_lanes = r.visited_lane_edges = -1;
             if (max_deg == 0)
                 for (int32_t v = lo; v < hi; ++v) max_deg = std::max<long long>(max_deg, g->h_row_ptr[v + 1] - g->h_row_ptr[v]);
             r.max_degree = max_deg;
@@ -513,6 +510,14 @@ gbbc_status run_batch_once(gbbc_graph* g, const BatchDesc& b, cudaStream_t st, b
         const long long new_n = new_hi - q_hi, new_e = (long long)s.hctr->edge_sum;
         if (tr) {
             gbbc_level_trace& r = g->trace[rec];
+            long long vl = 0, vle = 0;
+            for (int i = 0; i <= level && i < (int)nl.size(); ++i) {
+                vl += nl[i];
+                vle += nle[i];
+            }
+            r.frontier_lanes = level < (int)nl.size() ? nl[level] : -1;
+            r.visited_lanes = vl;
+            r.visited_lane_edges = vle;
             r.next_vertices = new_n;
             r.next_edges = new_e;
             r.scanned_edges = pull ? (long long)s.hctr->scanned : 0;

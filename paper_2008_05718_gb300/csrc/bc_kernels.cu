@@ -760,11 +760,23 @@ __device__ __forceinline__ u128 psi_term(u64 bits, int eoff, int Ev) {
     return shl_term(M, e + Ev + 12);
 }
 
+// Lane-compacted accumulation.  A round of up to four contributing
+// successors (slot u = 0..3, lanes f_u) is expanded into a list of
+// (slot, lane) terms, and each thread of the warp takes one term: it loads
+// psi[w_u][lane], shifts it to the lane's fixed point and adds it into
+// acc[u][lane] in shared memory.  Lanes are distinct within a slot, so the
+// adds need no atomics; the four slots are summed when the row is done.
+struct BwdWarpSmem {
+    u64 acc[4][kLanes][2];
+    int E[kLanes];
+    unsigned char list[4 * kLanes];
+};
+
 template <int NT, bool WIDE>
 __device__ __forceinline__ void bwd_gather_row(const Csr& g, const Slot& s, const MaskTag* Fs, int level, u64 m,
-                                               int32_t beg, int32_t end, int first, int E0, int E1, u128& a0,
-                                               u128& a1) {
+                                               int32_t beg, int32_t end, int first, BwdWarpSmem& sm) {
     const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
     for (int32_t base = beg + first * kWarp; base < end; base += NT * kWarp) {
         int32_t p = base + lane;
         int32_t w = 0;
@@ -778,24 +790,68 @@ __device__ __forceinline__ void bwd_gather_row(const Csr& g, const Slot& s, cons
         while (bal) {
             Round4 r;
             take_round(bal, w, f, r);
-            u64 b0[4], b1[4];
-            int x0[4], x1[4];
+            int K = 0;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                size_t at = (size_t)r.v[u] * kLanes;
-                bool q0 = (r.f[u] >> lane) & 1ull, q1 = (r.f[u] >> (lane + 32)) & 1ull;
-                b0[u] = q0 ? __ldg(s.psi + at + lane) : 0ull;
-                b1[u] = q1 ? __ldg(s.psi + at + lane + 32) : 0ull;
-                x0[u] = (WIDE && q0) ? __ldg(s.psi_e + at + lane) : 0;
-                x1[u] = (WIDE && q1) ? __ldg(s.psi_e + at + lane + 32) : 0;
+                unsigned lo = (unsigned)r.f[u], hi = (unsigned)(r.f[u] >> 32);
+                int clo = __popc(lo);
+                if ((lo >> lane) & 1u) sm.list[K + __popc(lo & below)] = (unsigned char)((u << 6) | lane);
+                if ((hi >> lane) & 1u) sm.list[K + clo + __popc(hi & below)] = (unsigned char)((u << 6) | (lane + 32));
+                K += clo + __popc(hi);
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if ((r.f[u] >> lane) & 1ull) a0 = add128(a0, psi_term<WIDE>(b0[u], x0[u], E0));
-                if ((r.f[u] >> (lane + 32)) & 1ull) a1 = add128(a1, psi_term<WIDE>(b1[u], x1[u], E1));
+            __syncwarp();
+            for (int i = lane; i < K; i += kWarp) {
+                unsigned code = sm.list[i];
+                int u = (int)(code >> 6), j = (int)(code & 63u);
+                int32_t wv = u == 0 ? r.v[0] : (u == 1 ? r.v[1] : (u == 2 ? r.v[2] : r.v[3]));
+                size_t at = (size_t)wv * kLanes + j;
+                u64 bits = __ldg(s.psi + at);
+                int xo = WIDE ? __ldg(s.psi_e + at) : 0;
+                u128 t = psi_term<WIDE>(bits, xo, sm.E[j]);
+                u64* a = sm.acc[u][j];
+                u128 cur = {a[0], a[1]};
+                cur = add128(cur, t);
+                a[0] = cur.lo;
+                a[1] = cur.hi;
             }
+            __syncwarp();
         }
     }
+}
+
+// Before a row: publish the lanes' exponents.  After it: the lanes' sums
+// (slots added) for this thread's two lanes, leaving the slots at zero.
+__device__ __forceinline__ void bwd_row_begin(BwdWarpSmem& sm, int E0, int E1) {
+    const int lane = threadIdx.x & 31;
+    sm.E[lane] = E0;
+    sm.E[lane + 32] = E1;
+    __syncwarp();
+}
+
+__device__ __forceinline__ void bwd_row_end(BwdWarpSmem& sm, u128& a0, u128& a1) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    a0.lo = a0.hi = a1.lo = a1.hi = 0ull;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        u128 x = {sm.acc[u][lane][0], sm.acc[u][lane][1]};
+        u128 y = {sm.acc[u][lane + 32][0], sm.acc[u][lane + 32][1]};
+        a0 = add128(a0, x);
+        a1 = add128(a1, y);
+        sm.acc[u][lane][0] = sm.acc[u][lane][1] = 0ull;
+        sm.acc[u][lane + 32][0] = sm.acc[u][lane + 32][1] = 0ull;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void bwd_smem_zero(BwdWarpSmem& sm) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        sm.acc[u][lane][0] = sm.acc[u][lane][1] = 0ull;
+        sm.acc[u][lane + 32][0] = sm.acc[u][lane + 32][1] = 0ull;
+    }
+    __syncwarp();
 }
 
 // per-lane finish: delta (returned, units 2^-64) and psi_v (stored)
@@ -854,8 +910,12 @@ __device__ __forceinline__ void lane_norms(const Slot& s, int32_t v, u64 m, u64&
 }
 
 template <bool WIDE>
-__global__ void k_bwd(Csr g, Slot s, u64* bc, long long q_lo, long long q_hi, int level, int heavy_deg) {
+__global__ void __launch_bounds__(kBlock) k_bwd(Csr g, Slot s, u64* bc, long long q_lo, long long q_hi, int level,
+                                               int heavy_deg) {
     const int lane = threadIdx.x & 31;
+    __shared__ BwdWarpSmem smem[kBlock / kWarp];
+    BwdWarpSmem& sm = smem[threadIdx.x >> 5];
+    bwd_smem_zero(sm);
     const MaskTag* Fs = s.F + (size_t)((level + 1) & 1) * s.n;
     MaskTag* Fo = s.F + (size_t)(level & 1) * s.n;
     for (long long e = q_lo + gwarp(); e < q_hi; e += nwarps()) {
@@ -876,8 +936,10 @@ __global__ void k_bwd(Csr g, Slot s, u64* bc, long long q_lo, long long q_hi, in
         u64 N0, N1;
         int E0, E1;
         lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
-        u128 a0 = {0ull, 0ull}, a1 = {0ull, 0ull};
-        bwd_gather_row<1, WIDE>(g, s, Fs, level, m, beg, end, 0, E0, E1, a0, a1);
+        u128 a0, a1;
+        bwd_row_begin(sm, E0, E1);
+        bwd_gather_row<1, WIDE>(g, s, Fs, level, m, beg, end, 0, sm);
+        bwd_row_end(sm, a0, a1);
         bwd_store<WIDE>(s, bc, v, m, E0, E1, N0, N1, a0, a1);
     }
 }
@@ -898,6 +960,9 @@ __global__ void k_bwd_tasks(Csr g, Slot s, int level) {
     constexpr int NW = kChunkBlock / kWarp;
     const MaskTag* Fs = s.F + (size_t)((level + 1) & 1) * s.n;
     __shared__ u128 ps[NW][kLanes];
+    __shared__ BwdWarpSmem smem[NW];
+    BwdWarpSmem& sm = smem[wid];
+    bwd_smem_zero(sm);
     const long long cnt = task_count(s);
     for (long long t = blockIdx.x; t < cnt; t += gridDim.x) {
         int h;
@@ -910,7 +975,9 @@ __global__ void k_bwd_tasks(Csr g, Slot s, int level) {
             u64 N0, N1;
             int E0, E1;
             lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
-            bwd_gather_row<NW, WIDE>(g, s, Fs, level, m, p0, p1, wid, E0, E1, a0, a1);
+            bwd_row_begin(sm, E0, E1);
+            bwd_gather_row<NW, WIDE>(g, s, Fs, level, m, p0, p1, wid, sm);
+            bwd_row_end(sm, a0, a1);
         }
         ps[wid][lane] = a0;
         ps[wid][lane + 32] = a1;
