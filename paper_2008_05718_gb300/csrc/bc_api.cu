@@ -36,6 +36,8 @@ struct gbbc_graph {
     bool wide_sticky = false;        // batches start in the wide sigma format
     Slot slot;
     bool slot_ready = false;
+    PlainState plain;            // batch width 1
+    bool plain_ready = false;
     gbbc_options opt;
     std::string err;
     std::vector<std::pair<void*, size_t>> allocs;
@@ -271,7 +273,7 @@ gbbc_status alloc_slot(gbbc_graph* g) {
     CK(g, cudaMemset(s.hcarry, 0, (size_t)hcap * sizeof(u64)));
     CKS(dalloc_t(g, &s.ctr, 1));
     CKS(dalloc_t(g, &s.d_src, kLanes));
-    CK(g, cudaMallocHost((void**)&s.hctr, sizeof(Counters)));
+    if (!s.hctr) CK(g, cudaMallocHost((void**)&s.hctr, sizeof(Counters)));
     CK(g, cudaMemset(s.nx, 0, n * sizeof(u64)));
     g->slot_ready = true;
     return GBBC_OK;
@@ -595,6 +597,72 @@ gbbc_status run_batch_once(gbbc_graph* g, const BatchDesc& b, cudaStream_t st, b
     return GBBC_OK;
 }
 
+gbbc_status alloc_plain(gbbc_graph* g) {
+    if (g->plain_ready) return GBBC_OK;
+    PlainState& p = g->plain;
+    size_t n = (size_t)std::max<int32_t>(g->n, 1);
+    p.n = g->n;
+    CKS(dalloc_t(g, &p.dist, n));
+    CKS(dalloc_t(g, &p.sigma, n));
+    CKS(dalloc_t(g, &p.psi, n));
+    CKS(dalloc_t(g, &p.queue, n));
+    CKS(dalloc_t(g, &p.heavy, n));
+    CKS(dalloc_t(g, &p.ctr, 1));
+    if (!g->slot.hctr) CK(g, cudaMallocHost((void**)&g->slot.hctr, sizeof(Counters)));
+    g->plain_ready = true;
+    return GBBC_OK;
+}
+
+// One source through the plain path (level-synchronous, per-level kernels).
+gbbc_status run_plain(gbbc_graph* g, int32_t src, int32_t lo, int32_t hi, long long index, cudaStream_t st) {
+    PlainState& p = g->plain;
+    Counters* hc = g->slot.hctr;
+    Csr c{g->n, g->nnz, g->d_row_ptr, g->d_col};
+    const size_t rn = (size_t)(hi - lo);
+    const int hd = g->opt.heavy_degree;
+    CK(g, cudaMemsetAsync(p.dist + lo, 0xff, rn * sizeof(int32_t), st));
+    CK(g, cudaMemsetAsync(p.sigma + lo, 0, rn * sizeof(u64), st));
+    std::memset(hc, 0, sizeof(Counters));
+    hc->qtail = 1;
+    CK(g, cudaMemcpyAsync(p.ctr, hc, sizeof(Counters), cudaMemcpyHostToDevice, st));
+    launch_plain_seed(p, src, st);
+    g->stats.kernel_launches++;
+    std::vector<long long> off = {0, 1};
+    int level = 0;
+    for (;;) {
+        CK(g, cudaMemsetAsync(&p.ctr->heavy, 0, sizeof(unsigned long long), st));
+        launch_plain_fwd(c, p, off[level], off[level + 1], level, hd, g->nsm, st);
+        g->stats.kernel_launches += 2;
+        g->stats.levels_push++;
+        CK(g, cudaGetLastError());
+        CK(g, cudaMemcpyAsync(hc, p.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        CK(g, cudaStreamSynchronize(st));
+        long long nh = (long long)hc->qtail;
+        if (nh == off[level + 1]) break;
+        off.push_back(nh);
+        ++level;
+    }
+    const int nlev = level + 1;
+    g->stats.levels_fwd += nlev;
+    if (hc->carry)
+        return fail(g, GBBC_ERR_CAPACITY,
+                    "plain path (batch width 1): a shortest-path count reached 2^64; use batch width 32 or 64");
+    if (g->k_dist) {
+        size_t at = (size_t)index * (size_t)g->n + (size_t)lo;
+        CK(g, cudaMemcpyAsync(g->k_dist + at, p.dist + lo, rn * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        CK(g, cudaMemcpyAsync(g->k_sigma + at, p.sigma + lo, rn * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+    }
+    for (int l = nlev - 1; l >= 1; --l) {
+        CK(g, cudaMemsetAsync(&p.ctr->heavy, 0, sizeof(unsigned long long), st));
+        launch_plain_bwd(c, p, g->d_bc, off[l], off[l + 1], l, hd, g->nsm, st);
+        g->stats.kernel_launches += 2;
+    }
+    CK(g, cudaGetLastError());
+    g->stats.batches++;
+    g->stats.sources++;
+    return GBBC_OK;
+}
+
 gbbc_status alloc_keep(gbbc_graph* g, long long k, cudaStream_t st) {
     dfree(g, g->k_dist);
     dfree(g, g->k_sigma);
@@ -620,9 +688,15 @@ gbbc_status alloc_keep(gbbc_graph* g, long long k, cudaStream_t st) {
 gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
                          cudaStream_t st) {
     long long k = (long long)gsrc.size();
-    CKS(alloc_slot(g));
     CKS(alloc_keep(g, k, st));
     g->last_stream = st;
+    if (g->opt.batch_width == 1) {  // plain: one source at a time, list order
+        CKS(alloc_plain(g));
+        for (long long i = 0; i < k; ++i)
+            CKS(run_plain(g, gsrc[i], (int32_t)g->goff[gid[i]], (int32_t)g->goff[gid[i] + 1], i, st));
+        return GBBC_OK;
+    }
+    CKS(alloc_slot(g));
     // group by graph (stable), then pack up to 64 consecutive sources
     std::vector<long long> order(k);
     for (long long i = 0; i < k; ++i) order[i] = i;

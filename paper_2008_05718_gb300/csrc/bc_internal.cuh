@@ -88,6 +88,17 @@ struct Slot {
     int32_t* d_src = nullptr;// [64] sources of the batch
 };
 
+// Device state of the plain one-source-at-a-time path (batch width 1).
+struct PlainState {
+    int32_t n = 0;
+    int32_t* dist = nullptr;   // [n]
+    u64* sigma = nullptr;      // [n]
+    u64* psi = nullptr;        // [n] (1 + delta) / sigma as double bits
+    int32_t* queue = nullptr;  // [n] vertices by level
+    int32_t* heavy = nullptr;  // [n] rows deferred to the block-per-row kernels
+    Counters* ctr = nullptr;
+};
+
 struct Csr {
     int32_t n;
     long long nnz;
@@ -111,6 +122,11 @@ void launch_keep_dist(const Slot& s, long long q_lo, long long q_hi, int level, 
 void launch_keep_sigma(const Slot& s, int32_t lo, int32_t hi, uint64_t* sigma, uint8_t* ovf, long long n_total,
                        long long first_src, int nsrc, cudaStream_t st);
 void launch_undo(const Slot& s, long long q_lo, long long q_hi, cudaStream_t st);
+void launch_plain_seed(const PlainState& p, int32_t src, cudaStream_t st);
+void launch_plain_fwd(const Csr& g, const PlainState& p, long long q_lo, long long q_hi, int level, int heavy_deg,
+                      int nsm, cudaStream_t st);
+void launch_plain_bwd(const Csr& g, const PlainState& p, u64* bc, long long q_lo, long long q_hi, int level,
+                      int heavy_deg, int nsm, cudaStream_t st);
 void launch_validate(const Csr& g, int32_t* flags, cudaStream_t st);
 void launch_fill_i32(int32_t* p, long long count, int32_t value, cudaStream_t st);
 void launch_offset_copy(const int32_t* src, int32_t* dst, long long count, int32_t add, cudaStream_t st);

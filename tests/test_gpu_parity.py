@@ -267,3 +267,23 @@ def test_bc_bit_identical_across_schedules(gb):
     runs.append(run_gpu(gb, g, S[::-1].copy())[0])  # other batch composition
     for r in runs[1:]:
         assert np.array_equal(r, runs[0])
+
+
+# ---- the plain one-source-at-a-time path (batch width 1) ---------------------
+
+@pytest.mark.parametrize("make", [lambda: gg.workload("er4096")[0], lambda: gg.rmat(12, 16, seed=23),
+                                  lambda: gg.from_edges(9, [(0, 1), (1, 2), (4, 5), (5, 6), (6, 4)])])
+def test_plain_path_parity_and_identical_bits(gb, make):
+    g = make()
+    S = gg.sample_sources(g.n, min(g.n, 97), seed=23)
+    got, _ = check(gb, g, S, keep=(0, len(S) - 1), batch_width=1)
+    batched, _, _ = run_gpu(gb, g, S, batch_width=64)
+    assert np.array_equal(got, batched)  # same integer arithmetic, same bits
+
+
+def test_plain_path_rejects_wide_counts(gb):
+    g = gg.diamond_chain(70)
+    with gb.BC.from_graph(g, batch_width=1) as bc:
+        with pytest.raises(gb.GbbcError) as e:
+            bc.compute([0])
+        assert e.value.status == gb.GBBC_ERR_CAPACITY
