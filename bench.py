@@ -215,7 +215,13 @@ def run_ours(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     opts = dict(batch_width=args.width, policy=args.policy)
 
+    weights = None
+    if args.policy in ("auto", "learned") and args.width != 1:
+        from paper_2008_05718_gb300 import policy as pol
+        weights = pol.shipped_weights()
     bc = gbbc.BC.from_csr(g.n, rp, col, stream=stream, **opts)
+    if weights is not None:
+        bc.load_policy(weights)
 
     def step():
         bc.reset()
@@ -259,6 +265,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         with gbbc.BC.from_csr(g.n, rp_h, col_h, stream=stream, **opts) as h:
+            if weights is not None:
+                h.load_policy(weights)
             h.compute(src_h, stream=stream)
             h.read(out_h, stream=stream)
     torch.cuda.synchronize()
@@ -269,6 +277,8 @@ def run_ours(args):
 
     # ---- roofline of the dominant step kind (one traced step) ----
     with gbbc.BC.from_csr(g.n, rp, col, stream=stream, flags=gbbc.GBBC_TRACE, **opts) as tb:
+        if weights is not None:
+            tb.load_policy(weights)
         tb.compute(src, stream=stream)
         tb.sync()
         prof = tb.profile()
@@ -297,7 +307,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "sources": k,
-                           "n": g.n, "nnz": g.nnz, "batch_width": args.width, "policy": args.policy,
+                           "n": g.n, "nnz": g.nnz, "batch_width": args.width,
+                           "policy": args.policy + (" (learned, shipped weights)" if weights is not None else ""),
                            "l2": "flushed between timed steps (512 MiB device write)"},
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,

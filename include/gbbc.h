@@ -206,6 +206,10 @@ typedef struct gbbc_level_trace {
     float ms_pull;              /* bottom-up discovery time */
     float ms_gather;            /* sigma gather of level l+1 */
     float ms_backward;          /* backward step of level l+1 */
+    float features[6];          /* direction-policy features of this step:
+                                   log-scaled frontier popcount, frontier edge
+                                   sum, unvisited (vertex, lane) pairs, level,
+                                   degree mean, degree max (see bc_policy_eval) */
 } gbbc_level_trace;
 
 /* Copy up to max records into out; *count receives the number available. */
@@ -228,6 +232,56 @@ typedef struct gbbc_kernel_profile {
 } gbbc_kernel_profile;
 
 gbbc_status bc_get_profile(const gbbc_graph* g, gbbc_kernel_profile* out, int32_t max, int32_t* count);
+
+/*
+ * Learned direction policy.  A multilayer perceptron 6 -> 32 -> 32 -> K
+ * (ReLU hidden layers) with FP32 parameters laid out as W1[32][6], b1[32],
+ * W2[32][32], b2[32], W3[K][32], b3[K].  For the direction head K = 2
+ * (logits of top-down push and bottom-up pull; the larger wins).  Its inputs
+ * are the six features of gbbc_level_trace.features.  The network only
+ * chooses the schedule: BC, dist and sigma do not depend on it.  The paper
+ * has no learned component; its nearest analogue is choosing the CPU:GPU
+ * split from measured run times (Sec. V-C).
+ *
+ * bc_mlp_* run on the device: params, x (n x 6, row-major), target, weight,
+ * out, grad, loss pointers are DEVICE memory (FP32); they synchronize the
+ * stream before returning.
+ */
+int64_t bc_mlp_param_count(int32_t k_out);  /* -1 if k_out is not 1 or 2 */
+
+/* out[n][k_out] = network(x) in FP32. */
+gbbc_status bc_mlp_forward(const float* params, int32_t k_out, const float* x, int64_t n, float* out, void* stream);
+
+/*
+ * Loss and its gradient over n samples (full batch).  loss_kind 0: softmax
+ * cross-entropy with target[i] the class index (k_out = 2); loss_kind 1:
+ * squared error against target[i] (k_out = 1).  Sample i is weighted by
+ * weight[i] / sum(weight) (weight may be NULL: equal weights).  grad has
+ * bc_mlp_param_count(k_out) entries; *loss_out (device, may be NULL) gets
+ * the loss.  Sums over samples run in sample order: deterministic.
+ */
+gbbc_status bc_mlp_loss_grad(const float* params, int32_t k_out, const float* x, const float* target,
+                             const float* weight, int64_t n, int32_t loss_kind, float* grad, float* loss_out,
+                             void* stream);
+
+/* One Adam step (Kingma and Ba, ICLR 2015) with bias correction at step t >= 1. */
+gbbc_status bc_mlp_adam_step(float* params, const float* grad, float* m, float* v, int64_t count, float lr,
+                             float beta1, float beta2, float eps, int32_t t, void* stream);
+
+/* epochs of full-batch Adam (beta 0.9/0.999, eps 1e-8) from the given params;
+ * loss_history (device, may be NULL) receives the loss before each step. */
+gbbc_status bc_mlp_train(float* params, int32_t k_out, const float* x, const float* target, const float* weight,
+                         int64_t n, int32_t loss_kind, int32_t epochs, float lr, float* loss_history, void* stream);
+
+/* The level loop's inference path on n feature vectors: FP16 weights, FP32
+ * sums.  logits[n][2] and choice[n] (0 push, 1 pull) may be NULL. */
+gbbc_status bc_policy_eval(const float* params, const float* x, int64_t n, float* logits, int32_t* choice,
+                           void* stream);
+
+/* Load a direction network (FP32 params, host or device, bytes =
+ * bc_mlp_param_count(2) * 4) into the handle; GBBC_POLICY_AUTO then uses it
+ * and GBBC_POLICY_LEARNED requires it.  params == NULL unloads it. */
+gbbc_status bc_policy_load(gbbc_graph* g, const float* params, size_t bytes);
 
 /*
  * bc_compute_noalloc - BC of one small graph with no memory allocation.

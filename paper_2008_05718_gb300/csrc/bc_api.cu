@@ -21,6 +21,10 @@ using namespace gbbc;
 extern "C" const char* bc_status_string(gbbc_status s);
 extern "C" void bc_graph_destroy(gbbc_graph* g);
 extern "C" gbbc_status bc_clear_trace(gbbc_graph* g);
+extern "C" int64_t bc_mlp_param_count(int32_t k_out);
+namespace gbbc {
+cudaError_t policy_to_half(const float* params_dev, void* half_dev, cudaStream_t st);
+}
 
 struct gbbc_graph {
     int device = 0;
@@ -44,6 +48,9 @@ struct gbbc_graph {
     size_t bytes = 0;
     gbbc_stats stats;
     cudaStream_t last_stream = nullptr;
+    // learned direction policy (FP16 copy of the network) and per-graph stats
+    void* d_policy = nullptr;
+    std::vector<long long> graph_max_deg;
     // tracing (GBBC_TRACE)
     std::vector<gbbc_level_trace> trace;
     gbbc_kernel_profile prof[5];
@@ -289,36 +296,19 @@ gbbc_status alloc_wide(gbbc_graph* g) {
     return GBBC_OK;
 }
 
+int effective_policy(const gbbc_graph* g) {
+    int p = g->opt.policy;
+    if (p == GBBC_POLICY_AUTO) return g->d_policy ? GBBC_POLICY_LEARNED : GBBC_POLICY_BEAMER;
+    return p;
+}
+
 struct BatchDesc {
+    int32_t gi;         // graph index
     int32_t lo, hi;     // vertex range of the graph the sources belong to
     long long first;    // position of the first source in the call's list
     int nsrc;
     int32_t src[kLanes];
 };
-
-// Direction of the next forward step (threshold rule of Beamer et al.,
-// SC'12, on the batch's combined frontier): switch to bottom-up once the
-// frontier's edges exceed the unexplored edges / alpha, back to top-down
-// once the frontier holds fewer than n / beta vertices.
-struct DirState {
-    bool pull = false;
-    long long explored = 0;
-};
-
-bool choose_pull(const gbbc_graph* g, DirState& d, int level, long long m_f, long long n_f, long long n_range,
-                 long long nnz_range) {
-    int pol = g->opt.policy;
-    if (pol == GBBC_POLICY_PUSH) return false;
-    if (pol == GBBC_POLICY_PULL) return level >= 1;
-    const double alpha = 14.0, beta = 24.0;
-    long long m_u = std::max<long long>(nnz_range - d.explored, 1);
-    if (!d.pull) {
-        if ((double)m_f > (double)m_u / alpha) d.pull = true;
-    } else {
-        if ((double)n_f < (double)n_range / beta) d.pull = false;
-    }
-    return d.pull;
-}
 
 enum ProfKind { PK_PUSH = 0, PK_PULL = 1, PK_GATHER = 2, PK_BWD = 3, PK_INIT = 4, PK_COUNT = 5 };
 const char* kProfNames[PK_COUNT] = {"push", "pull", "gather", "backward", "init"};
@@ -395,6 +385,7 @@ gbbc_status run_batch_once(gbbc_graph* g, const BatchDesc& b, cudaStream_t st, b
     const int hd = g->opt.heavy_degree;
     const bool tr = (g->opt.flags & GBBC_TRACE) != 0;
     const bool both = tr && (g->opt.flags & GBBC_TRACE_BOTH) != 0;
+    const int policy = effective_policy(g);
     std::vector<Timed> pend;
     const long long batch_id = g->batch_counter++;
     auto mark = [&](cudaEvent_t* e) -> gbbc_status {
@@ -422,32 +413,38 @@ gbbc_status run_batch_once(gbbc_graph* g, const BatchDesc& b, cudaStream_t st, b
     long long deg0 = 0, lane_deg0 = 0;
     for (int32_t v : distinct) deg0 += g->h_row_ptr[v + 1] - g->h_row_ptr[v];
     for (int j = 0; j < b.nsrc; ++j) lane_deg0 += g->h_row_ptr[b.src[j] + 1] - g->h_row_ptr[b.src[j]];
+    const u64 lanes0 = (b.nsrc == 64) ? ~0ull : ((1ull << b.nsrc) - 1ull);
+    // the counters describe level 0 for the first decision
     std::memset(s.hctr, 0, sizeof(Counters));
     s.hctr->qtail = (unsigned long long)nq0;
+    s.hctr->edge_sum = (unsigned long long)deg0;
+    s.hctr->lane_sum = (unsigned long long)b.nsrc;
+    s.hctr->lanes = lanes0;
     CK(g, cudaMemcpyAsync(s.ctr, s.hctr, sizeof(Counters), cudaMemcpyHostToDevice, st));
     launch_seed(s, b.nsrc, st);
-    g->stats.kernel_launches++;
+    const long long nnz_range = (long long)g->h_row_ptr[hi] - g->h_row_ptr[lo];
+    const long long n_range = hi - lo;
+    const double nr = (double)n_range;
+    const long long max_deg = g->graph_max_deg[b.gi];
+    launch_decide(s, 0, 0, policy, g->d_policy, n_range, nnz_range, max_deg, st);
+    g->stats.kernel_launches += 2;
     CK(g, cudaGetLastError());
     CKS(mark(&e1));
     if (tr) pend.push_back({PK_INIT, e0, e1, -1, -1, (double)rn * (8 * 3 + 32), true});
+    CK(g, cudaMemcpyAsync(s.hctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(g, cudaStreamSynchronize(st));
 
     // per-level sizes: entries, degree sum, (vertex, lane) pairs, pairs * degree
     std::vector<long long> off = {0, nq0}, nv = {nq0}, ne = {deg0}, nl = {b.nsrc}, nle = {lane_deg0};
     std::vector<long long> trace_rec;  // trace record of each level's step
-    const long long nnz_range = (long long)g->h_row_ptr[hi] - g->h_row_ptr[lo];
-    const long long n_range = hi - lo;
-    const double nr = (double)n_range;
-    long long max_deg = 0;
-    u64 lanes = (b.nsrc == 64) ? ~0ull : ((1ull << b.nsrc) - 1ull);
-    DirState dir;
+    u64 lanes = lanes0;
     int level = 0;
     const size_t disc_off = offsetof(Counters, heavy), disc_bytes = offsetof(Counters, err) - disc_off;
     const size_t gath_off = offsetof(Counters, lane_sum), gath_bytes = offsetof(Counters, medium) - gath_off;
     for (;;) {
         const long long q_lo = off[level], q_hi = off[level + 1];
         const long long m_f = ne[level];
-        bool pull = choose_pull(g, dir, level, m_f, nv[level], n_range, nnz_range);
-        dir.explored += m_f;
+        const bool pull = s.hctr->dir != 0;
         long long rec = -1;
         if (tr) {
             gbbc_level_trace r;
@@ -460,11 +457,16 @@ gbbc_status run_batch_once(gbbc_graph* g, const BatchDesc& b, cudaStream_t st, b
             r.nnz_range = nnz_range;
             r.frontier_vertices = nv[level];
             r.frontier_edges = ne[level];
-            // lane counts of this level arrive with this step's read-back
-            r.frontier_lanes = r.visited_lanes = r.visited_lane_edges = -1;
-            if (max_deg == 0)
-                for (int32_t v = lo; v < hi; ++v) max_deg = std::max<long long>(max_deg, g->h_row_ptr[v + 1] - g->h_row_ptr[v]);
+            r.frontier_lanes = nl[level];
+            long long vl = 0, vle = 0;
+            for (int i = 0; i <= level; ++i) {
+                vl += nl[i];
+                vle += nle[i];
+            }
+            r.visited_lanes = vl;
+            r.visited_lane_edges = vle;
             r.max_degree = max_deg;
+            for (int i = 0; i < 6; ++i) r.features[i] = s.hctr->feat[i];
             r.ms_push = r.ms_pull = r.ms_gather = r.ms_backward = -1.f;
             rec = (long long)g->trace.size();
             g->trace.push_back(r);
@@ -479,9 +481,10 @@ gbbc_status run_batch_once(gbbc_graph* g, const BatchDesc& b, cudaStream_t st, b
             CKS(mark(&e1));
             pend.push_back({pull ? PK_PUSH : PK_PULL, e0, e1, rec, pull ? 0 : 1, 0.0, false});
             CK(g, cudaGetLastError());
-            CK(g, cudaMemcpyAsync(s.hctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+            Counters probe;
+            CK(g, cudaMemcpyAsync(&probe, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
             CK(g, cudaStreamSynchronize(st));
-            launch_undo(s, q_hi, (long long)s.hctr->qtail, st);
+            launch_undo(s, q_hi, (long long)probe.qtail, st);
             unsigned long long rewind = (unsigned long long)q_hi;
             CK(g, cudaMemcpyAsync(&s.ctr->qtail, &rewind, sizeof(rewind), cudaMemcpyHostToDevice, st));
             CK(g, cudaStreamSynchronize(st));
@@ -497,73 +500,56 @@ gbbc_status run_batch_once(gbbc_graph* g, const BatchDesc& b, cudaStream_t st, b
             g->stats.levels_push++;
             g->stats.kernel_launches += 2;
         }
-        CKS(mark(&e1));
+        cudaEvent_t d1;
+        CKS(mark(&d1));
+        // gather of the new level: its range ends at the device's qtail
+        CK(g, cudaMemsetAsync((char*)s.ctr + gath_off, 0, gath_bytes, st));
+        launch_fwd_gather(c, s, q_hi, level, hd, g->nsm, st, wide);
+        cudaEvent_t g1;
+        CKS(mark(&g1));
+        launch_decide(s, q_hi, level + 1, policy, g->d_policy, n_range, nnz_range, max_deg, st);
+        g->stats.kernel_launches += wide ? 3 : 4;
         CK(g, cudaGetLastError());
         CK(g, cudaMemcpyAsync(s.hctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
         CK(g, cudaStreamSynchronize(st));
         if (s.hctr->err)
             return fail(g, GBBC_ERR_CAPACITY, "queue capacity exceeded in the forward phase (flags %u)",
                         s.hctr->err);
-        if (level >= 1) {  // lane statistics of level `level` (from its gather)
-            nl.push_back((long long)s.hctr->lane_sum);
-            nle.push_back((long long)s.hctr->lane_esum);
-        }
         const long long new_hi = (long long)s.hctr->qtail;
         const long long new_n = new_hi - q_hi, new_e = (long long)s.hctr->edge_sum;
+        const long long new_l = (long long)s.hctr->lane_sum, new_le = (long long)s.hctr->lane_esum;
         if (tr) {
             gbbc_level_trace& r = g->trace[rec];
-            long long vl = 0, vle = 0;
-            for (int i = 0; i <= level && i < (int)nl.size(); ++i) {
-                vl += nl[i];
-                vle += nle[i];
-            }
-            r.frontier_lanes = level < (int)nl.size() ? nl[level] : -1;
-            r.visited_lanes = vl;
-            r.visited_lane_edges = vle;
             r.next_vertices = new_n;
             r.next_edges = new_e;
             r.scanned_edges = pull ? (long long)s.hctr->scanned : 0;
-            double bytes = pull ? 8.0 * nr + 4.0 * (double)s.hctr->scanned +
-                                      16.0 * dmin((double)s.hctr->scanned, nr) + 20.0 * (double)new_n
-                                : 20.0 * (double)nv[level] + 4.0 * (double)m_f + 8.0 * dmin((double)m_f, nr) +
-                                      20.0 * (double)new_n;
-            pend.push_back({pull ? PK_PULL : PK_PUSH, e0, e1, rec, pull ? 1 : 0, bytes, true});
+            double dbytes = pull ? 8.0 * nr + 4.0 * (double)s.hctr->scanned +
+                                       16.0 * dmin((double)s.hctr->scanned, nr) + 20.0 * (double)new_n
+                                 : 20.0 * (double)nv[level] + 4.0 * (double)m_f + 8.0 * dmin((double)m_f, nr) +
+                                       20.0 * (double)new_n;
+            pend.push_back({pull ? PK_PULL : PK_PUSH, e0, d1, rec, pull ? 1 : 0, dbytes, true});
+            double gbytes = 68.0 * (double)new_n + 4.0 * (double)new_e + 16.0 * dmin((double)new_e, nr) +
+                            8.0 * (double)nl[level] + 8.0 * (double)new_l;
+            if (new_n > 0) pend.push_back({PK_GATHER, d1, g1, rec, 2, gbytes, true});
             CKS(resolve(g, pend));
         }
         if (new_n == 0) break;  // no vertex reached at level+1
         off.push_back(new_hi);
         nv.push_back(new_n);
         ne.push_back(new_e);
+        nl.push_back(new_l);
+        nle.push_back(new_le);
         lanes = s.hctr->lanes;
-        CK(g, cudaMemsetAsync((char*)s.ctr + gath_off, 0, gath_bytes, st));
-        CKS(mark(&e0));
-        launch_fwd_gather(c, s, q_hi, new_hi, level, hd, g->nsm, st, wide);
-        CKS(mark(&e1));
-        g->stats.kernel_launches += wide ? 2 : 3;
-        CK(g, cudaGetLastError());
-        if (tr) {
-            // sigma reads of level `level` + writes of level+1 (lane counts of
-            // level+1 arrive with the next read-back: bytes use level's count
-            // as the estimate and are corrected below)
-            double bytes = 68.0 * (double)new_n + 4.0 * (double)new_e + 16.0 * dmin((double)new_e, nr) +
-                           8.0 * (double)nl[level];
-            pend.push_back({PK_GATHER, e0, e1, rec, 2, bytes, true});
-        }
         ++level;
     }
     const int nlev = level + 1;  // levels 0 .. level
     g->stats.levels_fwd += nlev;
-    CK(g, cudaMemcpyAsync(s.hctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-    CK(g, cudaStreamSynchronize(st));
-    if (s.hctr->err) return fail(g, GBBC_ERR_CAPACITY, "row list overflow (flags %u)", s.hctr->err);
     if (s.hctr->carry && !wide) {  // rerun this batch in the wide format
         if (tr) CKS(resolve(g, pend));
         *need_wide = true;
         g->batch_counter--;
         return GBBC_OK;
     }
-    if (tr)  // sigma writes of each gathered level
-        for (int l = 1; l < nlev; ++l) g->prof[PK_GATHER].bytes += 8.0 * (double)nl[l];
     // ---- kept state for parity checks ----
     if (g->k_dist) {
         for (int l = 0; l < nlev; ++l)
@@ -688,6 +674,8 @@ gbbc_status alloc_keep(gbbc_graph* g, long long k, cudaStream_t st) {
 gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
                          cudaStream_t st) {
     long long k = (long long)gsrc.size();
+    if (g->opt.policy == GBBC_POLICY_LEARNED && !g->d_policy && g->opt.batch_width != 1)
+        return fail(g, GBBC_ERR_STATE, "GBBC_POLICY_LEARNED needs weights (bc_policy_load)");
     CKS(alloc_keep(g, k, st));
     g->last_stream = st;
     if (g->opt.batch_width == 1) {  // plain: one source at a time, list order
@@ -708,6 +696,7 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
     while (i < k) {
         BatchDesc b;
         int32_t gi = gid[order[i]];
+        b.gi = gi;
         b.lo = (int32_t)g->goff[gi];
         b.hi = (int32_t)g->goff[gi + 1];
         b.first = order[i];
@@ -727,6 +716,11 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
 
 gbbc_status finish_create(gbbc_graph* g, cudaStream_t st) {
     bc_clear_trace(g);
+    size_t count = g->goff.size() - 1;
+    g->graph_max_deg.assign(count, 0);
+    for (size_t i = 0; i < count; ++i)
+        for (long long v = g->goff[i]; v < g->goff[i + 1]; ++v)
+            g->graph_max_deg[i] = std::max<long long>(g->graph_max_deg[i], g->h_row_ptr[v + 1] - g->h_row_ptr[v]);
     size_t n1 = (size_t)std::max<int32_t>(g->n, 1);
     CKS(dalloc_t(g, &g->d_bc, 2 * n1));
     CKS(dalloc_t(g, &g->d_bc_out, n1));
@@ -955,6 +949,26 @@ gbbc_status bc_last_error_detail(const gbbc_graph* g, char* buf, size_t len) {
     if (!buf || len == 0) return GBBC_ERR_INVALID;
     std::snprintf(buf, len, "%s", g ? g->err.c_str() : tl_create_err.c_str());
     return GBBC_OK;
+}
+
+gbbc_status bc_policy_load(gbbc_graph* g, const float* params, size_t bytes) {
+    if (!g) return GBBC_ERR_INVALID;
+    const size_t want = (size_t)bc_mlp_param_count(2) * sizeof(float);
+    if (!params) {  // unload
+        if (g->d_policy) dfree(g, g->d_policy);
+        g->d_policy = nullptr;
+        return GBBC_OK;
+    }
+    if (bytes != want) return fail(g, GBBC_ERR_INVALID, "policy weights: %zu bytes, expected %zu", bytes, want);
+    float* tmp = nullptr;
+    CKS(dalloc(g, (void**)&tmp, want));
+    gbbc_status r = to_device(g, tmp, params, want, g->last_stream);
+    if (r == GBBC_OK && !g->d_policy) r = dalloc(g, &g->d_policy, (want / sizeof(float)) * 2);
+    if (r == GBBC_OK && policy_to_half(tmp, g->d_policy, g->last_stream) != cudaSuccess)
+        r = fail(g, GBBC_ERR_CUDA, "policy conversion failed");
+    if (r == GBBC_OK && cudaStreamSynchronize(g->last_stream) != cudaSuccess) r = fail(g, GBBC_ERR_CUDA, "sync");
+    dfree(g, tmp);
+    return r;
 }
 
 gbbc_status bc_get_trace(const gbbc_graph* g, gbbc_level_trace* out, int64_t max, int64_t* count) {

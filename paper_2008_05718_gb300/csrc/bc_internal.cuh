@@ -55,6 +55,13 @@ struct __align__(16) Counters {
     u64 lanes;                    // discovery: OR of the lanes reaching them
     unsigned err;                 // bit 0: queue overflow, bit 1: row list overflow
     unsigned carry;               // some sigma reached 2^64 in this batch
+    // direction decision (k_decide), state kept across the levels of a batch
+    unsigned long long visited;   // (vertex, lane) pairs reached so far
+    unsigned long long explored;  // frontier edges already expanded (threshold rule)
+    int dir;                      // decision for the next step: 0 push, 1 pull
+    int pull_state;               // threshold rule hysteresis
+    float feat[6];                // policy features of the decided step
+    float logit[2];               // MLP outputs (push, pull) when learned
 };
 
 // Device state of one batch slot (sized for n vertices, 64 lanes).
@@ -112,8 +119,8 @@ void launch_push(const Csr& g, const Slot& s, long long q_lo, long long q_hi, in
                  int nsm, cudaStream_t st);
 void launch_pull(const Csr& g, const Slot& s, int32_t lo, int32_t hi, u64 lanes, int level, int heavy_deg,
                  int nsm, cudaStream_t st);
-void launch_fwd_gather(const Csr& g, const Slot& s, long long q_lo, long long q_hi, int level, int heavy_deg,
-                       int nsm, cudaStream_t st, bool wide);
+void launch_fwd_gather(const Csr& g, const Slot& s, long long q_lo, int level, int heavy_deg, int nsm,
+                       cudaStream_t st, bool wide);
 void launch_bwd(const Csr& g, const Slot& s, u64* bc_fixed, long long q_lo, long long q_hi, int level,
                 int heavy_deg, int nsm, cudaStream_t st, bool wide);
 void launch_bc_to_double(const u64* bc_fixed, double* out, long long n, bool add, cudaStream_t st);
@@ -122,6 +129,9 @@ void launch_keep_dist(const Slot& s, long long q_lo, long long q_hi, int level, 
 void launch_keep_sigma(const Slot& s, int32_t lo, int32_t hi, uint64_t* sigma, uint8_t* ovf, long long n_total,
                        long long first_src, int nsrc, cudaStream_t st);
 void launch_undo(const Slot& s, long long q_lo, long long q_hi, cudaStream_t st);
+// Direction of the step at `level`, whose entries start at q_lo (end: qtail).
+void launch_decide(const Slot& s, long long q_lo, int level, int policy, const void* weights_fp16, long long n_range,
+                   long long nnz_range, long long max_deg, cudaStream_t st);
 void launch_plain_seed(const PlainState& p, int32_t src, cudaStream_t st);
 void launch_plain_fwd(const Csr& g, const PlainState& p, long long q_lo, long long q_hi, int level, int heavy_deg,
                       int nsm, cudaStream_t st);

@@ -551,8 +551,9 @@ __device__ __forceinline__ void fwd_store(const Slot& s, int32_t w, u64 m, const
 }
 
 template <bool WIDE>
-__global__ void k_fwd_gather(Csr g, Slot s, long long q_lo, long long q_hi, int level, int heavy_deg) {
+__global__ void k_fwd_gather(Csr g, Slot s, long long q_lo, int level, int heavy_deg) {
     const int lane = threadIdx.x & 31;
+    const long long q_hi = (long long)s.ctr->qtail;  // end of the entries the discovery queued
     const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
     MaskTag* Fn = s.F + (size_t)((level + 1) & 1) * s.n;
     unsigned long long lsum = 0, lesum = 0;
@@ -715,15 +716,14 @@ __global__ void k_fwd_gather_finish(Slot s) {
     }
 }
 
-void launch_fwd_gather(const Csr& g, const Slot& s, long long q_lo, long long q_hi, int level, int heavy_deg,
-                       int nsm, cudaStream_t st, bool wide) {
-    long long cnt = q_hi - q_lo;
-    if (cnt <= 0) return;
+void launch_fwd_gather(const Csr& g, const Slot& s, long long q_lo, int level, int heavy_deg, int nsm,
+                       cudaStream_t st, bool wide) {
+    // the entry count is known on the device only: a full grid, grid-stride
     if (wide) {
-        k_fwd_gather<true><<<grid_for(cnt, nsm), kBlock, 0, st>>>(g, s, q_lo, q_hi, level, heavy_deg);
+        k_fwd_gather<true><<<nsm * 8, kBlock, 0, st>>>(g, s, q_lo, level, heavy_deg);
         k_fwd_gather_heavy_wide<<<nsm * 2, kHeavyBlock, 0, st>>>(g, s, level);
     } else {
-        k_fwd_gather<false><<<grid_for(cnt, nsm), kBlock, 0, st>>>(g, s, q_lo, q_hi, level, heavy_deg);
+        k_fwd_gather<false><<<nsm * 8, kBlock, 0, st>>>(g, s, q_lo, level, heavy_deg);
         k_fwd_gather_tasks<<<nsm * 4, kChunkBlock, 0, st>>>(g, s, level);
         k_fwd_gather_finish<<<nsm, kBlock, 0, st>>>(s);
     }

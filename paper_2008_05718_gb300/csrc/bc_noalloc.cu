@@ -189,7 +189,7 @@ extern "C" gbbc_status bc_compute_noalloc(int32_t n, int64_t nnz, const int32_t*
             if (level + 2 > kNoallocMaxVertices + 1) return GBBC_ERR_CAPACITY;
             off[level + 2] = new_hi;
             NA_CK(cudaMemsetAsync((char*)s.ctr + gath_off, 0, gath_bytes, st));
-            launch_fwd_gather(c, s, q_hi, new_hi, level, heavy_deg, nsm, st, false);
+            launch_fwd_gather(c, s, q_hi, level, heavy_deg, nsm, st, false);
             NA_CK(cudaGetLastError());
             ++level;
         }

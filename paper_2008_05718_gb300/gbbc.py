@@ -29,7 +29,8 @@ GBBC_TRACE_BOTH = 4
 EXPORTS = ("bc_options_init", "bc_graph_create", "bc_graph_create_multi", "bc_compute", "bc_compute_multi",
            "bc_read", "bc_read_source_state", "bc_reset", "bc_sync", "bc_graph_destroy", "bc_status_string",
            "bc_last_error_detail", "bc_get_stats", "bc_get_trace", "bc_clear_trace", "bc_get_profile",
-           "bc_compute_noalloc")
+           "bc_compute_noalloc", "bc_mlp_param_count", "bc_mlp_forward", "bc_mlp_loss_grad", "bc_mlp_adam_step",
+           "bc_mlp_train", "bc_policy_eval", "bc_policy_load")
 NOALLOC_MAX_VERTICES = 16384
 
 
@@ -57,7 +58,8 @@ class gbbc_level_trace(ctypes.Structure):
                 ("visited_lane_edges", ctypes.c_int64), ("max_degree", ctypes.c_int64),
                 ("next_vertices", ctypes.c_int64), ("next_edges", ctypes.c_int64),
                 ("scanned_edges", ctypes.c_int64), ("ms_push", ctypes.c_float), ("ms_pull", ctypes.c_float),
-                ("ms_gather", ctypes.c_float), ("ms_backward", ctypes.c_float)]
+                ("ms_gather", ctypes.c_float), ("ms_backward", ctypes.c_float),
+                ("features", ctypes.c_float * 6)]
 
 
 class gbbc_kernel_profile(ctypes.Structure):
@@ -101,6 +103,14 @@ def load():
             "bc_clear_trace": (ctypes.c_int, [vp]),
             "bc_get_profile": (ctypes.c_int, [vp, P(gbbc_kernel_profile), i32, P(i32)]),
             "bc_compute_noalloc": (ctypes.c_int, [i32, i64, vp, vp, vp, i64, vp, vp]),
+            "bc_mlp_param_count": (i64, [i32]),
+            "bc_mlp_forward": (ctypes.c_int, [vp, i32, vp, i64, vp, vp]),
+            "bc_mlp_loss_grad": (ctypes.c_int, [vp, i32, vp, vp, vp, i64, i32, vp, vp, vp]),
+            "bc_mlp_adam_step": (ctypes.c_int, [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                                ctypes.c_float, i32, vp]),
+            "bc_mlp_train": (ctypes.c_int, [vp, i32, vp, vp, vp, i64, i32, i32, ctypes.c_float, vp, vp]),
+            "bc_policy_eval": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
+            "bc_policy_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -278,14 +288,17 @@ TRACE_FIELDS = [f for f, _ in gbbc_level_trace._fields_]
 
 
 def bc_get_trace(handle) -> dict:
-    """Per-level trace records as a dict of numpy arrays (one entry per field)."""
+    """Per-level trace records as a dict of numpy arrays (one entry per field;
+    "features" is an [n, 6] float32 array)."""
     lib = load()
     cnt = ctypes.c_int64()
     _check(lib.bc_get_trace(handle, None, 0, ctypes.byref(cnt)), handle)
     arr = (gbbc_level_trace * max(cnt.value, 1))()
     _check(lib.bc_get_trace(handle, arr, cnt.value, ctypes.byref(cnt)), handle)
     recs = arr[: cnt.value]
-    return {f: np.array([getattr(r, f) for r in recs]) for f in TRACE_FIELDS}
+    out = {f: np.array([getattr(r, f) for r in recs]) for f in TRACE_FIELDS if f != "features"}
+    out["features"] = np.array([list(r.features) for r in recs], np.float32).reshape(-1, 6)
+    return out
 
 
 def bc_clear_trace(handle):
@@ -300,6 +313,82 @@ def bc_get_profile(handle) -> dict:
     _check(lib.bc_get_profile(handle, arr, 16, ctypes.byref(cnt)), handle)
     return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes}
             for i in range(cnt.value)}
+
+
+# ---- learned direction policy ------------------------------------------------
+
+def bc_mlp_param_count(k_out=2):
+    return int(load().bc_mlp_param_count(int(k_out)))
+
+
+def _dev_f32(t):
+    import torch
+    return torch.as_tensor(t, dtype=torch.float32).cuda().contiguous()
+
+
+def bc_mlp_forward(params, x, k_out=2, stream=None):
+    """Network outputs [n, k_out] (FP32) for device or host inputs; returns a CUDA tensor."""
+    import torch
+    p, xs = _dev_f32(params), _dev_f32(x).reshape(-1, 6)
+    out = torch.zeros(xs.shape[0], k_out, dtype=torch.float32, device=xs.device)
+    _check(load().bc_mlp_forward(p.data_ptr(), k_out, xs.data_ptr(), xs.shape[0], out.data_ptr(), _stream(stream)))
+    return out
+
+
+def bc_mlp_loss_grad(params, x, target, weight=None, k_out=2, loss_kind=0, stream=None):
+    """(loss, grad) of the weighted loss over all samples."""
+    import torch
+    p, xs, ts = _dev_f32(params), _dev_f32(x).reshape(-1, 6), _dev_f32(target)
+    ws = _dev_f32(weight) if weight is not None else None
+    grad = torch.zeros_like(p)
+    loss = torch.zeros(1, dtype=torch.float32, device=p.device)
+    _check(load().bc_mlp_loss_grad(p.data_ptr(), k_out, xs.data_ptr(), ts.data_ptr(),
+                                   ws.data_ptr() if ws is not None else None, xs.shape[0], loss_kind,
+                                   grad.data_ptr(), loss.data_ptr(), _stream(stream)))
+    return float(loss.item()), grad
+
+
+def bc_mlp_adam_step(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """In-place Adam step on CUDA float32 tensors."""
+    _check(load().bc_mlp_adam_step(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), params.numel(),
+                                   lr, beta1, beta2, eps, int(t), _stream(stream)))
+
+
+def bc_mlp_train(params, x, target, weight=None, k_out=2, loss_kind=0, epochs=500, lr=3e-3, stream=None):
+    """Train in place on the device; returns (params tensor, loss history)."""
+    import torch
+    p, xs, ts = _dev_f32(params), _dev_f32(x).reshape(-1, 6), _dev_f32(target)
+    ws = _dev_f32(weight) if weight is not None else None
+    hist = torch.zeros(max(int(epochs), 1), dtype=torch.float32, device=p.device)
+    _check(load().bc_mlp_train(p.data_ptr(), k_out, xs.data_ptr(), ts.data_ptr(),
+                               ws.data_ptr() if ws is not None else None, xs.shape[0], loss_kind, int(epochs),
+                               float(lr), hist.data_ptr(), _stream(stream)))
+    return p, hist[: int(epochs)].cpu().numpy()
+
+
+def bc_policy_eval(params, x, stream=None):
+    """Inference path of the level loop (FP16 weights, FP32 sums): (logits, choice)."""
+    import torch
+    p, xs = _dev_f32(params), _dev_f32(x).reshape(-1, 6)
+    n = xs.shape[0]
+    logits = torch.zeros(n, 2, dtype=torch.float32, device=p.device)
+    choice = torch.zeros(n, dtype=torch.int32, device=p.device)
+    _check(load().bc_policy_eval(p.data_ptr(), xs.data_ptr(), n, logits.data_ptr(), choice.data_ptr(),
+                                 _stream(stream)))
+    return logits.cpu().numpy(), choice.cpu().numpy()
+
+
+def bc_policy_load(handle, params):
+    """Load FP32 direction-network parameters (numpy or tensor) into a handle; None unloads."""
+    if params is None:
+        _check(load().bc_policy_load(handle, None, 0), handle)
+        return
+    if hasattr(params, "data_ptr"):
+        t = params.to(dtype=__import__("torch").float32).contiguous()
+        _check(load().bc_policy_load(handle, t.data_ptr(), t.numel() * 4), handle)
+    else:
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load().bc_policy_load(handle, a.ctypes.data, a.nbytes), handle)
 
 
 def bc_compute_noalloc(n, nnz, row_ptr, col, sources, bc_out, stream=None):
@@ -380,6 +469,10 @@ class BC:
 
     def clear_trace(self):
         bc_clear_trace(self.h)
+
+    def load_policy(self, params):
+        bc_policy_load(self.h, params)
+        return self
 
     def close(self):
         if self.h:
