@@ -85,7 +85,21 @@ typedef struct gbbc_options {
                               thread block; 0 = default */
     int64_t mem_limit_bytes; /* 0 = no limit; else allocations beyond this
                                 many bytes fail with GBBC_ERR_OOM */
+    int32_t schedule;      /* enum gbbc_schedule */
+    int32_t reserved;
 } gbbc_options;
+
+/* How batches are mapped to the GPU. */
+enum gbbc_schedule {
+    GBBC_SCHEDULE_AUTO = 0,  /* autotuned: the first batches of the first call
+                                are timed in both modes, the faster one is kept
+                                for the handle (results identical either way) */
+    GBBC_SCHEDULE_GRID = 1,  /* one batch at a time on the whole GPU, a kernel
+                                per level step, host read-back per level */
+    GBBC_SCHEDULE_BLOCK = 2  /* one thread block per batch, many batches at
+                                once, one persistent launch per call; the level
+                                loop runs on the device (block barriers only) */
+};
 
 /* Fill *opt with defaults (auto width, auto policy, no validation). */
 void bc_options_init(gbbc_options* opt);
@@ -176,6 +190,8 @@ typedef struct gbbc_stats {
     int64_t device_bytes;   /* device memory held by the handle */
     int32_t batch_width;    /* width in use */
     int32_t policy;         /* policy in use */
+    int32_t schedule;       /* schedule in use (after autotuning) */
+    int32_t block_slots;    /* concurrent batches of the block schedule */
 } gbbc_stats;
 
 gbbc_status bc_get_stats(const gbbc_graph* g, gbbc_stats* out);

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -51,6 +53,16 @@ struct gbbc_graph {
     // learned direction policy (FP16 copy of the network) and per-graph stats
     void* d_policy = nullptr;
     std::vector<long long> graph_max_deg;
+    long long* d_graph_max_deg = nullptr;
+    // block-per-batch schedule
+    BlockSlots blk;
+    BlockBatch* d_bb = nullptr;
+    long long d_bb_cap = 0;
+    int32_t* d_bsrc = nullptr;
+    long long d_bsrc_cap = 0;
+    unsigned* d_next = nullptr;
+    unsigned long long* d_bstats = nullptr;
+    int tuned_schedule = 0;  // autotuner's choice (0: not tuned yet)
     // tracing (GBBC_TRACE)
     std::vector<gbbc_level_trace> trace;
     gbbc_kernel_profile prof[5];
@@ -195,6 +207,8 @@ gbbc_status read_options(gbbc_graph* g, const gbbc_options* opt) {
     if (o.policy < GBBC_POLICY_AUTO || o.policy > GBBC_POLICY_PULL)
         return fail(g, GBBC_ERR_INVALID, "unknown policy %d", o.policy);
     if (o.heavy_degree < 0) return fail(g, GBBC_ERR_INVALID, "heavy_degree must be >= 0");
+    if (o.schedule < GBBC_SCHEDULE_AUTO || o.schedule > GBBC_SCHEDULE_BLOCK)
+        return fail(g, GBBC_ERR_INVALID, "unknown schedule %d", o.schedule);
     if (g->opt.heavy_degree == 0) g->opt.heavy_degree = 1024;
     if (g->opt.heavy_degree < 32) g->opt.heavy_degree = 32;
     return GBBC_OK;
@@ -669,6 +683,8 @@ gbbc_status alloc_keep(gbbc_graph* g, long long k, cudaStream_t st) {
     return GBBC_OK;
 }
 
+gbbc_status dispatch(gbbc_graph* g, const std::vector<BatchDesc>& bs, cudaStream_t st);
+
 // Shared by bc_compute and bc_compute_multi: `gsrc` are whole-handle vertex
 // ids, `gid` their graph index.
 gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
@@ -684,14 +700,12 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
             CKS(run_plain(g, gsrc[i], (int32_t)g->goff[gid[i]], (int32_t)g->goff[gid[i] + 1], i, st));
         return GBBC_OK;
     }
-    CKS(alloc_slot(g));
     // group by graph (stable), then pack up to 64 consecutive sources
     std::vector<long long> order(k);
     for (long long i = 0; i < k; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](long long a, long long b) { return gid[a] < gid[b]; });
-    // KEEP_STATE writes rows by batch lane position, so keep list order
-    // whenever state is kept (sources are then required to be contiguous
-    // per graph, which holds for single-graph handles)
+    std::vector<BatchDesc> batches;
+    const int width = g->opt.batch_width == 32 ? 32 : kLanes;
     long long i = 0;
     while (i < k) {
         BatchDesc b;
@@ -702,15 +716,152 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
         b.first = order[i];
         b.nsrc = 0;
         bool contiguous = true;
-        while (i < k && b.nsrc < kLanes && gid[order[i]] == gi) {
+        while (i < k && b.nsrc < width && gid[order[i]] == gi) {
             if (order[i] != b.first + b.nsrc) contiguous = false;
             b.src[b.nsrc++] = gsrc[order[i]];
             ++i;
         }
+        // KEEP_STATE writes rows by the batch lane's position in the list
         if (g->k_dist && !contiguous)
             return fail(g, GBBC_ERR_INVALID, "GBBC_KEEP_STATE needs the sources of each graph to be contiguous");
-        CKS(run_batch(g, b, st));
+        batches.push_back(b);
     }
+    return dispatch(g, batches, st);
+}
+
+// ---- block-per-batch schedule ----------------------------------------------
+
+gbbc_status alloc_block(gbbc_graph* g, long long nslot, int want) {
+    BlockSlots& S = g->blk;
+    if (S.count >= want && S.nslot >= nslot) return GBBC_OK;
+    // release the old slots
+    for (void* p : {(void*)S.vis, (void*)S.nx, (void*)S.ovf, (void*)S.F, (void*)S.sigma, (void*)S.psi, (void*)S.sN,
+                    (void*)S.sX, (void*)S.psi_e, (void*)S.qv, (void*)S.qm, (void*)S.lev, (void*)S.ctr})
+        dfree(g, p);
+    S = BlockSlots();
+    const long long qcap = nslot * kLanes + kLanes;
+    const double per_slot = (double)nslot * (3 * 8 + 2 * sizeof(MaskTag) + kLanes * (8 + 8 + 8 + 4 + 4) + 8) +
+                            (double)qcap * 12 + sizeof(Counters);
+    size_t free_b = 0, total_b = 0;
+    CK(g, cudaMemGetInfo(&free_b, &total_b));
+    double budget = 0.5 * (double)free_b;
+    if (g->opt.mem_limit_bytes > 0) budget = std::min(budget, (double)g->opt.mem_limit_bytes - (double)g->bytes);
+    int count = (int)std::min<double>((double)want, std::floor(budget / per_slot));
+    if (count < 1) return fail(g, GBBC_ERR_OOM, "no room for one block-schedule slot (%.0f bytes)", per_slot);
+    const size_t ns = (size_t)nslot, c = (size_t)count;
+    S.nslot = nslot;
+    S.qcap = qcap;
+    S.count = count;
+    CKS(dalloc_t(g, &S.vis, c * ns));
+    CKS(dalloc_t(g, &S.nx, c * ns));
+    CKS(dalloc_t(g, &S.ovf, c * ns));
+    CKS(dalloc_t(g, &S.F, c * 2 * ns));
+    CKS(dalloc_t(g, &S.sigma, c * ns * kLanes));
+    CKS(dalloc_t(g, &S.psi, c * ns * kLanes));
+    CKS(dalloc_t(g, &S.sN, c * ns * kLanes));
+    CKS(dalloc_t(g, &S.sX, c * ns * kLanes));
+    CKS(dalloc_t(g, &S.psi_e, c * ns * kLanes));
+    CKS(dalloc_t(g, &S.qv, c * (size_t)qcap));
+    CKS(dalloc_t(g, &S.qm, c * (size_t)qcap));
+    CKS(dalloc_t(g, &S.lev, c * (ns + 2)));
+    CKS(dalloc_t(g, &S.ctr, c));
+    return GBBC_OK;
+}
+
+gbbc_status run_block_mode(gbbc_graph* g, const BatchDesc* bs, int nb, cudaStream_t st) {
+    if (nb <= 0) return GBBC_OK;
+    long long nslot = 1;
+    std::vector<BlockBatch> hb((size_t)nb);
+    std::vector<int32_t> hsrc;
+    for (int i = 0; i < nb; ++i) {
+        nslot = std::max<long long>(nslot, (long long)bs[i].hi - bs[i].lo);
+        hb[i].gi = bs[i].gi;
+        hb[i].lo = bs[i].lo;
+        hb[i].hi = bs[i].hi;
+        hb[i].nsrc = bs[i].nsrc;
+        hb[i].src_off = (long long)hsrc.size();
+        hsrc.insert(hsrc.end(), bs[i].src, bs[i].src + bs[i].nsrc);
+    }
+    CKS(alloc_block(g, nslot, std::min(nb, g->nsm)));
+    if (g->d_bb_cap < nb) {
+        dfree(g, g->d_bb);
+        CKS(dalloc_t(g, &g->d_bb, (size_t)nb));
+        g->d_bb_cap = nb;
+    }
+    if (g->d_bsrc_cap < (long long)hsrc.size()) {
+        dfree(g, g->d_bsrc);
+        CKS(dalloc_t(g, &g->d_bsrc, hsrc.size()));
+        g->d_bsrc_cap = (long long)hsrc.size();
+    }
+    if (!g->d_next) CKS(dalloc_t(g, &g->d_next, 1));
+    if (!g->d_bstats) CKS(dalloc_t(g, &g->d_bstats, 4));
+    if (!g->d_graph_max_deg) {
+        CKS(dalloc_t(g, &g->d_graph_max_deg, g->graph_max_deg.size()));
+        CK(g, cudaMemcpy(g->d_graph_max_deg, g->graph_max_deg.data(), g->graph_max_deg.size() * sizeof(long long),
+                         cudaMemcpyHostToDevice));
+    }
+    CK(g, cudaMemcpyAsync(g->d_bb, hb.data(), hb.size() * sizeof(BlockBatch), cudaMemcpyHostToDevice, st));
+    CK(g, cudaMemcpyAsync(g->d_bsrc, hsrc.data(), hsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(g, cudaMemsetAsync(g->d_next, 0, sizeof(unsigned), st));
+    CK(g, cudaMemsetAsync(g->d_bstats, 0, 4 * sizeof(unsigned long long), st));
+    Csr c{g->n, g->nnz, g->d_row_ptr, g->d_col};
+    CK(g, launch_block_batches(c, g->blk, g->d_bb, nb, g->d_bsrc, g->d_next, g->d_bc, effective_policy(g),
+                               g->d_policy, g->d_graph_max_deg, g->d_bstats, g->wide_sticky, st));
+    g->stats.kernel_launches++;
+    unsigned long long hst[4];
+    CK(g, cudaMemcpyAsync(hst, g->d_bstats, sizeof(hst), cudaMemcpyDeviceToHost, st));
+    std::vector<Counters> hc((size_t)g->blk.count);
+    CK(g, cudaMemcpyAsync(hc.data(), g->blk.ctr, hc.size() * sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(g, cudaStreamSynchronize(st));
+    for (const Counters& x : hc)
+        if (x.err) return fail(g, GBBC_ERR_CAPACITY, "block schedule: queue capacity exceeded (flags %u)", x.err);
+    if ((int)hst[0] != nb) return fail(g, GBBC_ERR_CUDA, "block schedule ran %llu of %d batches", hst[0], nb);
+    g->stats.batches += nb;
+    for (int i = 0; i < nb; ++i) g->stats.sources += bs[i].nsrc;
+    g->stats.levels_fwd += (long long)hst[1];
+    g->stats.levels_pull += (long long)hst[2];
+    g->stats.levels_push += (long long)(hst[1] - hst[2]);
+    g->stats.wide_batches += g->wide_sticky ? (long long)nb : (long long)hst[3];
+    if (hst[3] > 0) g->wide_sticky = true;  // later batches start wide
+    g->stats.block_slots = g->blk.count;
+    return GBBC_OK;
+}
+
+double now_s() {
+    return (double)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch()).count() * 1e-9;
+}
+
+// Grid or block for each batch: fixed by the options, forced to grid when
+// per-level state is kept or traced, else autotuned once per handle from
+// timed runs of the call's first batches (whose results are kept).
+gbbc_status dispatch(gbbc_graph* g, const std::vector<BatchDesc>& bs, cudaStream_t st) {
+    const int nb = (int)bs.size();
+    int sched = g->opt.schedule;
+    if (g->k_dist || (g->opt.flags & GBBC_TRACE)) sched = GBBC_SCHEDULE_GRID;
+    if (sched == GBBC_SCHEDULE_AUTO && g->tuned_schedule) sched = g->tuned_schedule;
+    int done = 0;
+    if (sched == GBBC_SCHEDULE_AUTO && nb >= 2) {
+        CKS(alloc_slot(g));
+        CK(g, cudaStreamSynchronize(st));
+        double t0 = now_s();
+        CKS(run_batch(g, bs[0], st));
+        CK(g, cudaStreamSynchronize(st));
+        double t_grid = now_s() - t0;
+        int nblk = std::min(nb - 1, g->nsm);
+        t0 = now_s();
+        CKS(run_block_mode(g, bs.data() + 1, nblk, st));
+        double t_block = (now_s() - t0) / nblk;
+        done = 1 + nblk;
+        g->tuned_schedule = t_block < t_grid ? GBBC_SCHEDULE_BLOCK : GBBC_SCHEDULE_GRID;
+        sched = g->tuned_schedule;
+    } else if (sched == GBBC_SCHEDULE_AUTO) {
+        sched = GBBC_SCHEDULE_GRID;
+    }
+    g->stats.schedule = sched;
+    if (sched == GBBC_SCHEDULE_BLOCK) return run_block_mode(g, bs.data() + done, nb - done, st);
+    CKS(alloc_slot(g));
+    for (int i = done; i < nb; ++i) CKS(run_batch(g, bs[i], st));
     return GBBC_OK;
 }
 
@@ -726,6 +877,7 @@ gbbc_status finish_create(gbbc_graph* g, cudaStream_t st) {
     CKS(dalloc_t(g, &g->d_bc_out, n1));
     CK(g, cudaMemsetAsync(g->d_bc, 0, 2 * n1 * sizeof(u64), st));
     g->stats.batch_width = g->opt.batch_width == 0 ? 64 : g->opt.batch_width;
+    g->stats.schedule = g->opt.schedule;
     g->stats.policy = g->opt.policy;
     CK(g, cudaStreamSynchronize(st));
     return GBBC_OK;

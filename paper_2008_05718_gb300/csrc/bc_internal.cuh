@@ -113,6 +113,37 @@ struct Csr {
     const int32_t* col;
 };
 
+// ---- block-per-batch mode ----
+// One thread block runs a whole batch (forward and backward) with block
+// barriers only; blocks take batches from a work list.  Slot k holds the
+// state of the batch that block k is running, indexed by vertex - lo of the
+// batch's graph, so slots are sized for the largest graph of the handle.
+constexpr int kBlockThreads = 512;
+
+struct BlockBatch {
+    int32_t gi, lo, hi, nsrc;
+    long long src_off;   // first source of the batch in the source array
+};
+
+struct BlockSlots {
+    long long nslot = 0;  // vertices per slot
+    long long qcap = 0;   // queue entries per slot
+    int count = 0;        // slots (= blocks of the launch)
+    u64* vis = nullptr;
+    u64* nx = nullptr;
+    u64* ovf = nullptr;
+    MaskTag* F = nullptr;     // [slot][2][nslot]
+    u64* sigma = nullptr;     // [slot][nslot][64]
+    u64* psi = nullptr;
+    u64* sN = nullptr;
+    int32_t* sX = nullptr;
+    int32_t* psi_e = nullptr;
+    int32_t* qv = nullptr;    // [slot][qcap]
+    u64* qm = nullptr;
+    long long* lev = nullptr; // [slot][nslot + 2] level boundaries
+    Counters* ctr = nullptr;  // [slot]
+};
+
 // ---- launch wrappers (bc_kernels.cu) ----
 void launch_seed(const Slot& s, int nsrc, cudaStream_t st);
 void launch_push(const Csr& g, const Slot& s, long long q_lo, long long q_hi, int level, int heavy_deg,
@@ -129,6 +160,13 @@ void launch_keep_dist(const Slot& s, long long q_lo, long long q_hi, int level, 
 void launch_keep_sigma(const Slot& s, int32_t lo, int32_t hi, uint64_t* sigma, uint8_t* ovf, long long n_total,
                        long long first_src, int nsrc, cudaStream_t st);
 void launch_undo(const Slot& s, long long q_lo, long long q_hi, cudaStream_t st);
+// Block-per-batch persistent kernel over `nb` batches; stats[0..3]: batches,
+// forward levels, bottom-up levels, wide reruns (device, accumulated).
+// start_wide runs every batch in the wide sigma format from the start.
+cudaError_t launch_block_batches(const Csr& g, const BlockSlots& S, const BlockBatch* batches, int nb,
+                                 const int32_t* srcs, unsigned* next, u64* bc, int policy, const void* weights_fp16,
+                                 const long long* graph_max_deg, unsigned long long* stats, bool start_wide,
+                                 cudaStream_t st);
 // Direction of the step at `level`, whose entries start at q_lo (end: qtail).
 void launch_decide(const Slot& s, long long q_lo, int level, int policy, const void* weights_fp16, long long n_range,
                    long long nnz_range, long long max_deg, cudaStream_t st);

@@ -15,6 +15,7 @@
 
 #include "bc_fixed.cuh"
 #include "bc_internal.cuh"
+#include "bc_policy.cuh"
 
 namespace gbbc {
 
@@ -47,6 +48,15 @@ __device__ __forceinline__ void warp_append(bool pred, int32_t item, unsigned lo
         else atomicOr(err, errbit);
     }
 }
+
+// Loads of slot data: NC = the data is read-only for the whole kernel (one
+// kernel per step), so the non-coherent path may serve it; the persistent
+// block kernel rewrites slot data between its own steps and uses L2-coherent
+// loads instead.
+template <bool NC>
+__device__ __forceinline__ u64 ldv(const u64* p) { return NC ? __ldg(p) : __ldcg(p); }
+template <bool NC>
+__device__ __forceinline__ int ldi(const int* p) { return NC ? __ldg(p) : __ldcg(p); }
 
 __device__ __forceinline__ long long gwarp() { return ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
 __device__ __forceinline__ long long nwarps() { return ((long long)gridDim.x * blockDim.x) >> 5; }
@@ -458,7 +468,7 @@ __device__ __forceinline__ void take_round(unsigned& bal, int32_t v, u64 f, Roun
     }
 }
 
-template <int NT, bool WIDE>
+template <int NT, bool WIDE, bool NC = true>
 __device__ __forceinline__ void fwd_gather_row(const Csr& g, const Slot& s, const MaskTag* F, int level, u64 m,
                                                int32_t beg, int32_t end, int first, GatherAcc& acc) {
     // this warp handles chunks starting at beg + first*32, stepping NT*32
@@ -482,13 +492,13 @@ __device__ __forceinline__ void fwd_gather_row(const Csr& g, const Slot& s, cons
                 const u64* row = s.sigma + (size_t)vv * kLanes;
                 u64 ov = s.ovf[vv];
                 if ((ff >> lane) & 1ull) {
-                    u64 x = __ldg(row + lane);
+                    u64 x = ldv<NC>(row + lane);
                     acc.a0 += x;
                     acc.c0 |= acc.a0 < x;
                     pred_term<WIDE>(s, vv, lane, x, ov, acc.w0);
                 }
                 if ((ff >> (lane + 32)) & 1ull) {
-                    u64 x = __ldg(row + lane + 32);
+                    u64 x = ldv<NC>(row + lane + 32);
                     acc.a1 += x;
                     acc.c1 |= acc.a1 < x;
                     pred_term<WIDE>(s, vv, lane + 32, x, ov, acc.w1);
@@ -502,8 +512,8 @@ __device__ __forceinline__ void fwd_gather_row(const Csr& g, const Slot& s, cons
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const u64* row = s.sigma + (size_t)r.v[u] * kLanes;
-                    x0[u] = ((r.f[u] >> lane) & 1ull) ? __ldg(row + lane) : 0ull;
-                    x1[u] = ((r.f[u] >> (lane + 32)) & 1ull) ? __ldg(row + lane + 32) : 0ull;
+                    x0[u] = ((r.f[u] >> lane) & 1ull) ? ldv<NC>(row + lane) : 0ull;
+                    x1[u] = ((r.f[u] >> (lane + 32)) & 1ull) ? ldv<NC>(row + lane + 32) : 0ull;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -772,7 +782,7 @@ struct BwdWarpSmem {
     unsigned char list[4 * kLanes];
 };
 
-template <int NT, bool WIDE>
+template <int NT, bool WIDE, bool NC = true>
 __device__ __forceinline__ void bwd_gather_row(const Csr& g, const Slot& s, const MaskTag* Fs, int level, u64 m,
                                                int32_t beg, int32_t end, int first, BwdWarpSmem& sm) {
     const int lane = threadIdx.x & 31;
@@ -805,8 +815,8 @@ __device__ __forceinline__ void bwd_gather_row(const Csr& g, const Slot& s, cons
                 int u = (int)(code >> 6), j = (int)(code & 63u);
                 int32_t wv = u == 0 ? r.v[0] : (u == 1 ? r.v[1] : (u == 2 ? r.v[2] : r.v[3]));
                 size_t at = (size_t)wv * kLanes + j;
-                u64 bits = __ldg(s.psi + at);
-                int xo = WIDE ? __ldg(s.psi_e + at) : 0;
+                u64 bits = ldv<NC>(s.psi + at);
+                int xo = WIDE ? ldi<NC>(s.psi_e + at) : 0;
                 u128 t = psi_term<WIDE>(bits, xo, sm.E[j]);
                 u64* a = sm.acc[u][j];
                 u128 cur = {a[0], a[1]};
@@ -879,7 +889,9 @@ __device__ __forceinline__ u128 shfl_xor128(u128 a, int o) {
     return r;
 }
 
-template <bool WIDE>
+__device__ __forceinline__ void atomic_add128(u64* a, u128 t);
+
+template <bool WIDE, bool ATOMIC_BC = false>
 __device__ __forceinline__ void bwd_store(const Slot& s, u64* bc, int32_t v, u64 m, int E0, int E1, u64 N0, u64 N1,
                                           u128 a0, u128 a1) {
     const int lane = threadIdx.x & 31;
@@ -890,12 +902,16 @@ __device__ __forceinline__ void bwd_store(const Slot& s, u64* bc, int32_t v, u64
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) c = add128(c, shfl_xor128(c, o));
     if (lane == 0) {
-        u128 b;
-        b.lo = bc[2 * (size_t)v];
-        b.hi = bc[2 * (size_t)v + 1];
-        b = add128(b, c);
-        bc[2 * (size_t)v] = b.lo;
-        bc[2 * (size_t)v + 1] = b.hi;
+        if (ATOMIC_BC) {  // several batches of one graph may run at once
+            atomic_add128(bc + 2 * (size_t)v, c);
+        } else {
+            u128 b;
+            b.lo = bc[2 * (size_t)v];
+            b.hi = bc[2 * (size_t)v + 1];
+            b = add128(b, c);
+            bc[2 * (size_t)v] = b.lo;
+            bc[2 * (size_t)v + 1] = b.hi;
+        }
     }
 }
 
@@ -1029,6 +1045,272 @@ void launch_bwd(const Csr& g, const Slot& s, u64* bc, long long q_lo, long long 
         k_bwd_tasks<false><<<nsm * 4, kChunkBlock, 0, st>>>(g, s, level);
         k_bwd_finish<false><<<nsm, kBlock, 0, st>>>(s, bc);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Block-per-batch mode.  The view of slot k for a batch of the graph whose
+// vertices are [lo, hi): every per-vertex array is offset by -lo, so the
+// row functions above index it with global vertex ids unchanged.
+__device__ __forceinline__ Slot slot_view(const BlockSlots& S, int k, int32_t lo) {
+    Slot v;
+    const long long base = (long long)k * S.nslot - lo;
+    v.n = (int32_t)S.nslot;  // parity stride of F
+    v.vis = S.vis + base;
+    v.nx = S.nx + base;
+    v.ovf = S.ovf + base;
+    v.F = S.F + (long long)k * 2 * S.nslot - lo;
+    v.sigma = S.sigma + base * kLanes;
+    v.psi = S.psi + base * kLanes;
+    v.sN = S.sN + base * kLanes;
+    v.sX = S.sX + base * kLanes;
+    v.psi_e = S.psi_e + base * kLanes;
+    v.qv = S.qv + (long long)k * S.qcap;
+    v.qm = S.qm + (long long)k * S.qcap;
+    v.qcap = S.qcap;
+    v.ctr = S.ctr + k;
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
+
+// One batch by the whole block.  Returns false when a count reached 2^64 in
+// the narrow format (the caller reruns the batch wide); BC is untouched then.
+template <bool WIDE>
+__device__ bool block_batch(const Csr& g, const Slot& s, long long* lev, const BlockBatch& bb, const int32_t* src,
+                            u64* bc, int policy, const __half* wts, float max_deg, BwdWarpSmem& sm, int* sh,
+                            unsigned long long* stats) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int32_t lo = bb.lo, hi = bb.hi;
+    const int nsrc = bb.nsrc;
+    const float n_range = (float)(hi - lo);
+    const float nnz_range = (float)(__ldg(g.row_ptr + hi) - __ldg(g.row_ptr + lo));
+    // ---- clear the slot's range and counters ----
+    for (int32_t v = lo + tid; v < hi; v += blockDim.x) {
+        s.vis[v] = 0ull;
+        s.nx[v] = 0ull;
+        s.ovf[v] = 0ull;
+        MaskTag t;
+        t.mask = 0ull;
+        t.tag = -1;
+        t.pad = 0;
+        s.F[v] = t;
+        s.F[s.n + v] = t;
+    }
+    if (tid < (int)(sizeof(Counters) / sizeof(unsigned))) ((unsigned*)s.ctr)[tid] = 0u;
+    if (tid < kLanes) sh[tid] = tid < nsrc ? src[tid] : -1;
+    __syncthreads();
+    // ---- seed: distinct sources form the level-0 queue (first-occurrence order) ----
+    u64 mask = 0ull;
+    bool fj = false;
+    if (tid < nsrc) {
+        fj = true;
+        for (int i = 0; i < nsrc; ++i)
+            if (sh[i] == sh[tid]) {
+                mask |= 1ull << i;
+                if (i < tid) fj = false;
+            }
+        sh[kLanes + tid] = fj ? 1 : 0;
+    }
+    __syncthreads();
+    if (tid < nsrc) {
+        int32_t v = sh[tid];
+        atomicOr(&s.vis[v], 1ull << tid);
+        s.sigma[(size_t)v * kLanes + tid] = 1ull;
+        if (fj) {
+            int pos = 0;
+            for (int i = 0; i < tid; ++i) pos += sh[kLanes + i];
+            s.qv[pos] = v;
+            s.qm[pos] = mask;
+            MaskTag t;
+            t.mask = mask;
+            t.tag = 0;
+            t.pad = 0;
+            s.F[v] = t;
+            atomicAdd(&s.ctr->qtail, 1ull);
+            atomicAdd(&s.ctr->edge_sum, (unsigned long long)(__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v)));
+        }
+    }
+    if (tid == 0) {
+        s.ctr->lane_sum = (unsigned long long)nsrc;
+        s.ctr->lanes = nsrc == 64 ? ~0ull : ((1ull << nsrc) - 1ull);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        lev[0] = 0;
+        lev[1] = (long long)ld_cg(&s.ctr->qtail);
+    }
+    if (wid == 0) decide_step(s.ctr, 0, 0, policy, wts, n_range, nnz_range, max_deg);
+    __syncthreads();
+    // ---- forward, level by level ----
+    int level = 0;
+    unsigned long long npull = 0;
+    for (;;) {
+        const long long q_lo = ld_cg(lev + level), q_hi = ld_cg(lev + level + 1);
+        const int dir = ld_cg(&s.ctr->dir);
+        const u64 lanes = ld_cg(&s.ctr->lanes);
+        __syncthreads();
+        if (tid == 0) {
+            s.ctr->heavy = s.ctr->tasks = s.ctr->medium = 0ull;
+            s.ctr->edge_sum = s.ctr->scanned = 0ull;
+            s.ctr->lanes = 0ull;
+        }
+        __syncthreads();
+        StepStats stats = {0ull, 0ull, 0ull};
+        if (!dir) {
+            for (long long e = q_lo + wid; e < q_hi; e += nw) {
+                int32_t v = s.qv[e];
+                u64 m = s.qm[e];
+                push_row(g, s, m, __ldg(g.row_ptr + v), __ldg(g.row_ptr + v + 1), lane, kWarp, stats);
+            }
+        } else {
+            ++npull;
+            const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
+            for (long long base = lo; base < hi; base += blockDim.x) {
+                int32_t w = (int32_t)(base + tid);
+                u64 u = w < hi ? (~s.vis[w] & lanes) : 0ull;
+                u64 f = 0ull;
+                int32_t beg = 0, end = 0;
+                if (u) {
+                    beg = __ldg(g.row_ptr + w);
+                    end = __ldg(g.row_ptr + w + 1);
+                    for (int32_t p = beg; p < end; ++p) {
+                        ++stats.scanned;
+                        MaskTag t = F[__ldg(g.col + p)];
+                        if (t.tag == level) {
+                            f |= t.mask;
+                            if ((f & u) == u) break;
+                        }
+                    }
+                }
+                u64 nm = f & u;
+                if (nm) {
+                    s.nx[w] = nm;
+                    stats.lanes |= nm;
+                    stats.esum += (unsigned long long)(end - beg);
+                }
+                warp_append(nm != 0ull, w, &s.ctr->qtail, s.qv, s.qcap, &s.ctr->err, 1u);
+            }
+        }
+        flush_stats(s, stats);
+        __syncthreads();
+        const long long new_hi = (long long)ld_cg(&s.ctr->qtail);
+        if (new_hi == q_hi || ld_cg(&s.ctr->err)) break;
+        if (tid == 0) {
+            s.ctr->lane_sum = s.ctr->lane_esum = 0ull;
+            lev[level + 2] = new_hi;
+        }
+        __syncthreads();
+        // ---- gather of level+1 (finalize masks, sigma sums) ----
+        {
+            const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
+            MaskTag* Fn = s.F + (size_t)((level + 1) & 1) * s.n;
+            unsigned long long lsum = 0;
+            for (long long e = q_hi + wid; e < new_hi; e += nw) {
+                int32_t w = s.qv[e];
+                u64 m = s.nx[w];
+                int32_t beg = __ldg(g.row_ptr + w), end = __ldg(g.row_ptr + w + 1);
+                __syncwarp();
+                if (lane == 0) {
+                    s.qm[e] = m;
+                    s.nx[w] = 0ull;
+                    s.vis[w] |= m;
+                    MaskTag t;
+                    t.mask = m;
+                    t.tag = level + 1;
+                    t.pad = 0;
+                    Fn[w] = t;
+                    lsum += (unsigned)__popcll(m);
+                }
+                GatherAcc acc;
+                gather_init(acc);
+                fwd_gather_row<1, WIDE, false>(g, s, F, level, m, beg, end, 0, acc);
+                fwd_store<WIDE>(s, w, m, acc);
+            }
+            if (lane == 0 && lsum) atomicAdd(&s.ctr->lane_sum, lsum);
+        }
+        __syncthreads();
+        if (wid == 0) decide_step(s.ctr, q_hi, level + 1, policy, wts, n_range, nnz_range, max_deg);
+        __syncthreads();
+        ++level;
+    }
+    const int nlev = level + 1;
+    if (tid == 0) {
+        atomicAdd(stats + 1, (unsigned long long)nlev);
+        atomicAdd(stats + 2, npull);
+    }
+    if (ld_cg(&s.ctr->err)) return true;  // reported by the host; BC is not trusted
+    if (!WIDE && ld_cg(&s.ctr->carry)) return false;
+    // ---- backward, levels nlev-1 .. 1 ----
+    for (int l = nlev - 1; l >= 1; --l) {
+        const long long q_lo = ld_cg(lev + l), q_hi = ld_cg(lev + l + 1);
+        const MaskTag* Fs = s.F + (size_t)((l + 1) & 1) * s.n;
+        MaskTag* Fo = s.F + (size_t)(l & 1) * s.n;
+        for (long long e = q_lo + wid; e < q_hi; e += nw) {
+            int32_t v = s.qv[e];
+            u64 m = s.qm[e];
+            if (lane == 0) {
+                MaskTag t;
+                t.mask = m;
+                t.tag = l;
+                t.pad = 0;
+                Fo[v] = t;
+            }
+            u64 N0, N1;
+            int E0, E1;
+            lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
+            u128 a0, a1;
+            bwd_row_begin(sm, E0, E1);
+            bwd_gather_row<1, WIDE, false>(g, s, Fs, l, m, __ldg(g.row_ptr + v), __ldg(g.row_ptr + v + 1), 0, sm);
+            bwd_row_end(sm, a0, a1);
+            bwd_store<WIDE, true>(s, bc, v, m, E0, E1, N0, N1, a0, a1);
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kBlockThreads) k_block_batches(Csr g, BlockSlots S, const BlockBatch* batches,
+                                                                 int nb, const int32_t* srcs, unsigned* next,
+                                                                 u64* bc, int policy, const __half* wts,
+                                                                 const long long* gmaxdeg,
+                                                                 unsigned long long* stats, int start_wide) {
+    extern __shared__ unsigned char dsm[];
+    BwdWarpSmem* smem = reinterpret_cast<BwdWarpSmem*>(dsm);
+    BwdWarpSmem& sm = smem[threadIdx.x >> 5];
+    __shared__ int sh[2 * kLanes + 1];
+    bwd_smem_zero(sm);
+    long long* lev = S.lev + (long long)blockIdx.x * (S.nslot + 2);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) sh[2 * kLanes] = (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int b = sh[2 * kLanes];
+        if (b >= nb) break;
+        const BlockBatch bb = batches[b];
+        const Slot v = slot_view(S, blockIdx.x, bb.lo);
+        const float md = (float)gmaxdeg[bb.gi];
+        __syncthreads();
+        if (start_wide || !block_batch<false>(g, v, lev, bb, srcs + bb.src_off, bc, policy, wts, md, sm, sh, stats)) {
+            __syncthreads();
+            if (threadIdx.x == 0 && !start_wide) atomicAdd(stats + 3, 1ull);
+            block_batch<true>(g, v, lev, bb, srcs + bb.src_off, bc, policy, wts, md, sm, sh, stats);
+        }
+        if (threadIdx.x == 0) atomicAdd(stats, 1ull);
+    }
+}
+
+cudaError_t launch_block_batches(const Csr& g, const BlockSlots& S, const BlockBatch* batches, int nb,
+                                 const int32_t* srcs, unsigned* next, u64* bc, int policy, const void* weights_fp16,
+                                 const long long* graph_max_deg, unsigned long long* stats, bool start_wide,
+                                 cudaStream_t st) {
+    const size_t smem = (size_t)(kBlockThreads / kWarp) * sizeof(BwdWarpSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_block_batches, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_block_batches<<<S.count, kBlockThreads, smem, st>>>(g, S, batches, nb, srcs, next, bc, policy,
+                                                          (const __half*)weights_fp16, graph_max_deg, stats,
+                                                          start_wide ? 1 : 0);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -23,58 +23,10 @@
 namespace gbbc {
 
 // ---------------------------------------------------------------------------
-// Decision for the step at `level`: entries [q_lo, qtail), degree sum
-// edge_sum, (vertex, lane) pairs lane_sum, active lanes `lanes`.
+// Decision for the step at `level` (see decide_step in bc_policy.cuh).
 __global__ void k_decide(Slot s, long long q_lo, int level, int policy, const __half* w, float n_range,
                          float nnz_range, float max_deg) {
-    Counters* c = s.ctr;
-    const int t = threadIdx.x;
-    __shared__ float x[kMlpIn];
-    unsigned long long nv = c->qtail - (unsigned long long)q_lo;
-    unsigned long long ne = c->edge_sum;
-    unsigned long long pairs = c->lane_sum;
-    unsigned long long visited = c->visited + pairs;
-    float active = (float)__popcll(c->lanes);
-    if (t == 0) {
-        float unvisited = active * n_range - (float)visited;
-        policy_features((float)pairs, (float)ne, unvisited, level, n_range, nnz_range, max_deg, x);
-    }
-    __syncwarp();
-    int dir = 0;
-    float out[2] = {0.f, 0.f};
-    if (policy == GBBC_POLICY_LEARNED && w) {
-        float xv[kMlpIn];
-#pragma unroll
-        for (int i = 0; i < kMlpIn; ++i) xv[i] = x[i];
-        mlp_warp_eval(w, 2, xv, out);
-        dir = out[1] > out[0] ? 1 : 0;
-    } else if (policy == GBBC_POLICY_PUSH) {
-        dir = 0;
-    } else if (policy == GBBC_POLICY_PULL) {
-        dir = level >= 1 ? 1 : 0;
-    } else {
-        // threshold rule: go bottom-up once the frontier's edges exceed the
-        // unexplored edges / alpha; return once the frontier holds fewer
-        // than n / beta vertices
-        const float alpha = 14.f, beta = 24.f;
-        float m_u = fmaxf(nnz_range - (float)c->explored, 1.f);
-        int st = c->pull_state;
-        if (!st) {
-            if ((float)ne > m_u / alpha) st = 1;
-        } else if ((float)nv < n_range / beta) {
-            st = 0;
-        }
-        dir = st;
-        if (t == 0) c->pull_state = st;
-    }
-    if (t == 0) {
-        c->dir = dir;
-        c->visited = visited;
-        c->explored += ne;
-        for (int i = 0; i < kMlpIn; ++i) c->feat[i] = x[i];
-        c->logit[0] = out[0];
-        c->logit[1] = out[1];
-    }
+    decide_step(s.ctr, q_lo, level, policy, w, n_range, nnz_range, max_deg);
 }
 
 void launch_decide(const Slot& s, long long q_lo, int level, int policy, const void* weights_fp16, long long n_range,

@@ -14,6 +14,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "bc_internal.cuh"
+
 namespace gbbc {
 
 constexpr int kMlpIn = 6;
@@ -61,6 +63,58 @@ __device__ __forceinline__ void policy_features(float pairs, float edges, float 
     x[3] = log2p1((float)level) / 8.f;
     x[4] = log2p1(nnz / (n > 0.f ? n : 1.f)) / 16.f;
     x[5] = log2p1(max_deg) / 24.f;
+}
+
+// Decision for the step at `level`, by one warp (all 32 threads call it):
+// entries [q_lo, c->qtail), degree sum c->edge_sum, (vertex, lane) pairs
+// c->lane_sum, active lanes c->lanes.  Writes c->dir, the features and the
+// running state (visited pairs, explored edges, threshold hysteresis).
+__device__ __forceinline__ void decide_step(Counters* c, long long q_lo, int level, int policy, const __half* w,
+                                            float n_range, float nnz_range, float max_deg) {
+    const int t = threadIdx.x & 31;
+    unsigned long long nv = c->qtail - (unsigned long long)q_lo;
+    unsigned long long ne = c->edge_sum;
+    unsigned long long pairs = c->lane_sum;
+    unsigned long long visited = c->visited + pairs;
+    float active = (float)__popcll(c->lanes);
+    float x[kMlpIn];
+    policy_features((float)pairs, (float)ne, active * n_range - (float)visited, level, n_range, nnz_range, max_deg,
+                    x);
+    int dir = 0;
+    float out[2] = {0.f, 0.f};
+    if (policy == GBBC_POLICY_LEARNED && w) {
+        mlp_warp_eval(w, 2, x, out);
+        dir = out[1] > out[0] ? 1 : 0;
+    } else if (policy == GBBC_POLICY_PUSH) {
+        dir = 0;
+    } else if (policy == GBBC_POLICY_PULL) {
+        dir = level >= 1 ? 1 : 0;
+    } else {
+        // threshold rule (Beamer, Asanovic, Patterson, SC'12): go bottom-up
+        // once the frontier's edges exceed the unexplored edges / alpha; come
+        // back once the frontier holds fewer than n / beta vertices
+        const float alpha = 14.f, beta = 24.f;
+        float m_u = fmaxf(nnz_range - (float)c->explored, 1.f);
+        int st = c->pull_state;
+        if (!st) {
+            if ((float)ne > m_u / alpha) st = 1;
+        } else if ((float)nv < n_range / beta) {
+            st = 0;
+        }
+        dir = st;
+    }
+    __syncwarp();
+    if (t == 0) {
+        if (!(policy == GBBC_POLICY_LEARNED && w) && policy != GBBC_POLICY_PUSH && policy != GBBC_POLICY_PULL)
+            c->pull_state = dir;
+        c->dir = dir;
+        c->visited = visited;
+        c->explored += ne;
+        for (int i = 0; i < kMlpIn; ++i) c->feat[i] = x[i];
+        c->logit[0] = out[0];
+        c->logit[1] = out[1];
+    }
+    __syncwarp();
 }
 
 }  // namespace gbbc

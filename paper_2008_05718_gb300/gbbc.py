@@ -21,6 +21,7 @@ _lib = None
 
 GBBC_OK, GBBC_ERR_INVALID, GBBC_ERR_OOM, GBBC_ERR_CUDA, GBBC_ERR_TIMEOUT, GBBC_ERR_CAPACITY, GBBC_ERR_STATE = range(7)
 POLICY = {"auto": 0, "beamer": 1, "learned": 2, "push": 3, "pull": 4}
+SCHEDULE = {"auto": 0, "grid": 1, "block": 2}
 GBBC_KEEP_STATE = 1
 GBBC_TRACE = 2
 GBBC_TRACE_BOTH = 4
@@ -37,14 +38,16 @@ NOALLOC_MAX_VERTICES = 16384
 class gbbc_options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("batch_width", ctypes.c_int32), ("policy", ctypes.c_int32),
                 ("validate", ctypes.c_int32), ("timeout_spins", ctypes.c_int64), ("flags", ctypes.c_uint32),
-                ("heavy_degree", ctypes.c_int32), ("mem_limit_bytes", ctypes.c_int64)]
+                ("heavy_degree", ctypes.c_int32), ("mem_limit_bytes", ctypes.c_int64),
+                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class gbbc_stats(ctypes.Structure):
     _fields_ = [("sources", ctypes.c_int64), ("batches", ctypes.c_int64), ("levels_fwd", ctypes.c_int64),
                 ("levels_push", ctypes.c_int64), ("levels_pull", ctypes.c_int64), ("wide_batches", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("batch_width", ctypes.c_int32), ("policy", ctypes.c_int32)]
+                ("batch_width", ctypes.c_int32), ("policy", ctypes.c_int32),
+                ("schedule", ctypes.c_int32), ("block_slots", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -172,7 +175,7 @@ def _as_i32(buf):
 
 
 def options(batch_width=0, policy="auto", validate=False, flags=0, heavy_degree=0, mem_limit_bytes=0,
-            timeout_spins=0) -> gbbc_options:
+            timeout_spins=0, schedule="auto") -> gbbc_options:
     o = gbbc_options()
     load().bc_options_init(ctypes.byref(o))
     o.batch_width = int(batch_width)
@@ -182,6 +185,7 @@ def options(batch_width=0, policy="auto", validate=False, flags=0, heavy_degree=
     o.heavy_degree = int(heavy_degree)
     o.mem_limit_bytes = int(mem_limit_bytes)
     o.timeout_spins = int(timeout_spins)
+    o.schedule = SCHEDULE[schedule] if isinstance(schedule, str) else int(schedule)
     return o
 
 

@@ -287,3 +287,45 @@ def test_plain_path_rejects_wide_counts(gb):
         with pytest.raises(gb.GbbcError) as e:
             bc.compute([0])
         assert e.value.status == gb.GBBC_ERR_CAPACITY
+
+
+# ---- the block-per-batch schedule and the autotuner --------------------------
+
+@pytest.mark.parametrize("make,k", [(lambda: gg.workload("er4096")[0], 300), (lambda: gg.rmat(12, 16, seed=61), 300),
+                                    (lambda: gg.grid(64, "0.05", seed=62), 200), (lambda: gg.diamond_chain(70), 211),
+                                    (lambda: gg.from_edges(7, [(0, 1), (1, 2), (4, 5)]), 7)])
+@pytest.mark.parametrize("policy", ["push", "beamer"])
+def test_block_schedule_parity_and_identical_bits(gb, make, k, policy):
+    g = make()
+    S = gg.sample_sources(g.n, min(k, g.n), seed=63)
+    want, _ = oracle.bc_graph(g, S)
+    blk, _, st = run_gpu(gb, g, S, schedule="block", policy=policy)
+    assert st["schedule"] == 2 and st["block_slots"] >= 1
+    assert_bc_close(blk, want)
+    grid, _, _ = run_gpu(gb, g, S, schedule="grid", policy=policy)
+    assert np.array_equal(blk, grid)
+
+
+def test_block_schedule_multi_graph_and_width32(gb):
+    graphs = [gg.rmat(10, 16, seed=71), gg.grid(40, "0.03", seed=72), gg.path(50), gg.rmat(11, 16, seed=73)]
+    gids, locs, per = [], [], []
+    for i, g in enumerate(graphs):
+        S = gg.sample_sources(g.n, min(g.n, 150), seed=74 + i)
+        per.append(S)
+        gids += [i] * len(S)
+        locs += list(S)
+    for width in (64, 32):
+        with gb.BC.from_graphs(graphs, schedule="block", batch_width=width) as bc:
+            bc.compute_multi(np.array(gids, np.int32), np.array(locs, np.int32))
+            for i, g in enumerate(graphs):
+                want, _ = oracle.bc_graph(g, per[i])
+                assert_bc_close(bc.read(graph_id=i), want)
+
+
+def test_autotuned_schedule_gives_identical_bits(gb):
+    g = gg.grid(80, "0.05", seed=81)
+    S = gg.sample_sources(g.n, 400, seed=81)
+    auto, _, st = run_gpu(gb, g, S, schedule="auto")
+    assert st["schedule"] in (1, 2)
+    grid, _, _ = run_gpu(gb, g, S, schedule="grid")
+    assert np.array_equal(auto, grid)
