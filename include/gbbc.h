@@ -152,6 +152,16 @@ gbbc_status bc_compute_multi(gbbc_graph* g, const int32_t* graph_id, const int32
 gbbc_status bc_read(gbbc_graph* g, double* bc_out, int32_t graph_id, void* stream);
 
 /*
+ * The accumulated BC in its exact internal form: 128-bit unsigned fixed
+ * point in units of 2^-64, as (low 64 bits, high 64 bits) pairs, 2 * n
+ * uint64 values (host or device).  Sums of these integers are exact and
+ * independent of order, so partial results computed on different GPUs (or
+ * calls) over disjoint source sets add up to bit-identical totals; round
+ * the sum to FP64 once, at the end.  graph_id as in bc_read.
+ */
+gbbc_status bc_read_fixed(gbbc_graph* g, uint64_t* out, int32_t graph_id, void* stream);
+
+/*
  * Per-source state of the last bc_compute, for sources in that call when
  * GBBC_KEEP_STATE was set: dist (int32[n], -1 unreachable), sigma (uint64[n],
  * number of shortest paths mod 2^64), overflow (uint8[n], 1 iff the true

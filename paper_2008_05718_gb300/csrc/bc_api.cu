@@ -1045,6 +1045,20 @@ gbbc_status bc_read(gbbc_graph* g, double* bc_out, int32_t graph_id, void* strea
     return GBBC_OK;
 }
 
+gbbc_status bc_read_fixed(gbbc_graph* g, uint64_t* out, int32_t graph_id, void* stream) {
+    if (!g) return GBBC_ERR_INVALID;
+    if (!out) return fail(g, GBBC_ERR_INVALID, "out is NULL");
+    int32_t count = (int32_t)g->goff.size() - 1;
+    if (graph_id < -1 || graph_id >= count) return fail(g, GBBC_ERR_INVALID, "graph_id %d", graph_id);
+    long long lo = graph_id < 0 ? 0 : g->goff[graph_id];
+    long long hi = graph_id < 0 ? g->n : g->goff[graph_id + 1];
+    cudaStream_t st = (cudaStream_t)stream;
+    if (hi > lo)
+        CK(g, cudaMemcpyAsync(out, g->d_bc + 2 * lo, (size_t)(hi - lo) * 2 * sizeof(u64), cudaMemcpyDefault, st));
+    CK(g, cudaStreamSynchronize(st));
+    return GBBC_OK;
+}
+
 gbbc_status bc_read_source_state(gbbc_graph* g, int64_t source_index, int32_t* dist, uint64_t* sigma,
                                  uint8_t* overflow) {
     if (!g) return GBBC_ERR_INVALID;

@@ -31,7 +31,7 @@ EXPORTS = ("bc_options_init", "bc_graph_create", "bc_graph_create_multi", "bc_co
            "bc_read", "bc_read_source_state", "bc_reset", "bc_sync", "bc_graph_destroy", "bc_status_string",
            "bc_last_error_detail", "bc_get_stats", "bc_get_trace", "bc_clear_trace", "bc_get_profile",
            "bc_compute_noalloc", "bc_mlp_param_count", "bc_mlp_forward", "bc_mlp_loss_grad", "bc_mlp_adam_step",
-           "bc_mlp_train", "bc_policy_eval", "bc_policy_load")
+           "bc_mlp_train", "bc_policy_eval", "bc_policy_load", "bc_read_fixed")
 NOALLOC_MAX_VERTICES = 16384
 
 
@@ -96,6 +96,7 @@ def load():
             "bc_compute_multi": (ctypes.c_int, [vp, vp, vp, i64, vp]),
             "bc_read": (ctypes.c_int, [vp, vp, i32, vp]),
             "bc_read_source_state": (ctypes.c_int, [vp, i64, vp, vp, vp]),
+            "bc_read_fixed": (ctypes.c_int, [vp, vp, i32, vp]),
             "bc_reset": (ctypes.c_int, [vp]),
             "bc_sync": (ctypes.c_int, [vp]),
             "bc_graph_destroy": (None, [vp]),
@@ -249,6 +250,13 @@ def bc_read(handle, n, out=None, graph_id=-1, stream=None):
         out = np.zeros(int(n), np.float64)
     p, keep = _ptr(out)
     _check(load().bc_read(handle, p, int(graph_id), _stream(stream)), handle)
+    return out
+
+
+def bc_read_fixed(handle, n, graph_id=-1, stream=None):
+    """Exact BC as uint64 [n, 2] (low, high words of 128-bit fixed point, units 2^-64)."""
+    out = np.zeros((int(n), 2), np.uint64)
+    _check(load().bc_read_fixed(handle, out.ctypes.data, int(graph_id), _stream(stream)), handle)
     return out
 
 
@@ -452,6 +460,10 @@ class BC:
     def read(self, out=None, graph_id=-1, stream=None):
         n = self.n if graph_id < 0 else int(self.offsets[graph_id + 1] - self.offsets[graph_id])
         return bc_read(self.h, n, out, graph_id, stream)
+
+    def read_fixed(self, graph_id=-1, stream=None):
+        n = self.n if graph_id < 0 else int(self.offsets[graph_id + 1] - self.offsets[graph_id])
+        return bc_read_fixed(self.h, n, graph_id, stream)
 
     def source_state(self, i):
         return bc_read_source_state(self.h, i, self.n)

@@ -329,3 +329,20 @@ def test_autotuned_schedule_gives_identical_bits(gb):
     assert st["schedule"] in (1, 2)
     grid, _, _ = run_gpu(gb, g, S, schedule="grid")
     assert np.array_equal(auto, grid)
+
+
+def test_fixed_point_partials_add_to_identical_bits(gb):
+    from paper_2008_05718_gb300 import multirank as mr
+    g = gg.rmat(12, 16, seed=91)
+    S = gg.sample_sources(g.n, 300, seed=91)
+    with gb.BC.from_graph(g) as bc:
+        bc.compute(S)
+        whole_fixed, whole = bc.read_fixed(), bc.read()
+    parts = []
+    for r in range(3):
+        with gb.BC.from_graph(g, schedule="block" if r % 2 else "grid") as bc:
+            bc.compute(mr.shard(S, r, 3))
+            parts.append(bc.read_fixed())
+    total = mr.sum_fixed(parts)
+    assert np.array_equal(total, whole_fixed)
+    assert np.array_equal(mr.fixed_to_double(total), whole)
