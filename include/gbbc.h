@@ -91,14 +91,17 @@ typedef struct gbbc_options {
 
 /* How batches are mapped to the GPU. */
 enum gbbc_schedule {
-    GBBC_SCHEDULE_AUTO = 0,  /* autotuned: the first batches of the first call
-                                are timed in both modes, the faster one is kept
-                                for the handle (results identical either way) */
+    GBBC_SCHEDULE_AUTO = 0,  /* batches of graphs above 65,536 vertices run
+                                grid; for the others the first call times its
+                                first batches in both modes (results kept) and
+                                the faster mode is kept for the handle; results
+                                are identical either way */
     GBBC_SCHEDULE_GRID = 1,  /* one batch at a time on the whole GPU, a kernel
                                 per level step, host read-back per level */
-    GBBC_SCHEDULE_BLOCK = 2  /* one thread block per batch, many batches at
-                                once, one persistent launch per call; the level
-                                loop runs on the device (block barriers only) */
+    GBBC_SCHEDULE_BLOCK = 2  /* one thread-block cluster (1 to 8 blocks) per
+                                batch, many batches at once, one persistent
+                                launch per call; the level loop runs on the
+                                device (cluster barriers only) */
 };
 
 /* Fill *opt with defaults (auto width, auto policy, no validation). */
@@ -200,7 +203,8 @@ typedef struct gbbc_stats {
     int64_t device_bytes;   /* device memory held by the handle */
     int32_t batch_width;    /* width in use */
     int32_t policy;         /* policy in use */
-    int32_t schedule;       /* schedule in use (after autotuning) */
+    int32_t schedule;       /* schedule of the last call (after autotuning;
+                               0 when it mixed both) */
     int32_t block_slots;    /* concurrent batches of the block schedule */
 } gbbc_stats;
 

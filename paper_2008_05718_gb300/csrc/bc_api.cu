@@ -736,7 +736,8 @@ gbbc_status alloc_block(gbbc_graph* g, long long nslot, int want) {
     if (S.count >= want && S.nslot >= nslot) return GBBC_OK;
     // release the old slots
     for (void* p : {(void*)S.vis, (void*)S.nx, (void*)S.ovf, (void*)S.F, (void*)S.sigma, (void*)S.psi, (void*)S.sN,
-                    (void*)S.sX, (void*)S.psi_e, (void*)S.qv, (void*)S.qm, (void*)S.lev, (void*)S.ctr})
+                    (void*)S.sX, (void*)S.psi_e, (void*)S.qv, (void*)S.qm, (void*)S.lev, (void*)S.ctr,
+                    (void*)S.slot_batch, S.lsp})
         dfree(g, p);
     S = BlockSlots();
     const long long qcap = nslot * kLanes + kLanes;
@@ -765,6 +766,8 @@ gbbc_status alloc_block(gbbc_graph* g, long long nslot, int want) {
     CKS(dalloc_t(g, &S.qm, c * (size_t)qcap));
     CKS(dalloc_t(g, &S.lev, c * (ns + 2)));
     CKS(dalloc_t(g, &S.ctr, c));
+    CKS(dalloc_t(g, &S.slot_batch, c));
+    CKS(dalloc(g, &S.lsp, c * (ns + 2)));
     return GBBC_OK;
 }
 
@@ -782,7 +785,12 @@ gbbc_status run_block_mode(gbbc_graph* g, const BatchDesc* bs, int nb, cudaStrea
         hb[i].src_off = (long long)hsrc.size();
         hsrc.insert(hsrc.end(), bs[i].src, bs[i].src + bs[i].nsrc);
     }
-    CKS(alloc_block(g, nslot, std::min(nb, g->nsm)));
+    // clusters: few batches get several SMs each (up to 8 CTAs, the portable
+    // cluster size), many batches one SM each
+    int csize = 1;
+    while (csize < 8 && (long long)nb * csize * 2 <= g->nsm) csize *= 2;
+    CKS(alloc_block(g, nslot, std::max(1, std::min(nb, g->nsm / csize))));
+    g->blk.csize = csize;
     if (g->d_bb_cap < nb) {
         dfree(g, g->d_bb);
         CKS(dalloc_t(g, &g->d_bb, (size_t)nb));
@@ -832,36 +840,56 @@ double now_s() {
                std::chrono::steady_clock::now().time_since_epoch()).count() * 1e-9;
 }
 
+// Graphs above this many vertices always run in the grid schedule: one
+// block per batch cannot hide the latency of their wide levels.
+constexpr long long kBlockMaxVertices = 65536;
+
 // Grid or block for each batch: fixed by the options, forced to grid when
-// per-level state is kept or traced, else autotuned once per handle from
-// timed runs of the call's first batches (whose results are kept).
+// per-level state is kept or traced.  Under GBBC_SCHEDULE_AUTO, batches of
+// graphs above kBlockMaxVertices run grid; the others run block unless a
+// timed trial (the call's first batches, whose results are kept: one in
+// grid, one wave in block) shows grid faster; the choice is kept per handle.
 gbbc_status dispatch(gbbc_graph* g, const std::vector<BatchDesc>& bs, cudaStream_t st) {
-    const int nb = (int)bs.size();
     int sched = g->opt.schedule;
     if (g->k_dist || (g->opt.flags & GBBC_TRACE)) sched = GBBC_SCHEDULE_GRID;
-    if (sched == GBBC_SCHEDULE_AUTO && g->tuned_schedule) sched = g->tuned_schedule;
-    int done = 0;
-    if (sched == GBBC_SCHEDULE_AUTO && nb >= 2) {
-        CKS(alloc_slot(g));
-        CK(g, cudaStreamSynchronize(st));
-        double t0 = now_s();
-        CKS(run_batch(g, bs[0], st));
-        CK(g, cudaStreamSynchronize(st));
-        double t_grid = now_s() - t0;
-        int nblk = std::min(nb - 1, g->nsm);
-        t0 = now_s();
-        CKS(run_block_mode(g, bs.data() + 1, nblk, st));
-        double t_block = (now_s() - t0) / nblk;
-        done = 1 + nblk;
-        g->tuned_schedule = t_block < t_grid ? GBBC_SCHEDULE_BLOCK : GBBC_SCHEDULE_GRID;
-        sched = g->tuned_schedule;
-    } else if (sched == GBBC_SCHEDULE_AUTO) {
-        sched = GBBC_SCHEDULE_GRID;
+    std::vector<BatchDesc> small, large;
+    if (sched == GBBC_SCHEDULE_AUTO) {
+        for (const BatchDesc& b : bs) ((long long)b.hi - b.lo > kBlockMaxVertices ? large : small).push_back(b);
+    } else {
+        (sched == GBBC_SCHEDULE_BLOCK ? small : large) = bs;
     }
-    g->stats.schedule = sched;
-    if (sched == GBBC_SCHEDULE_BLOCK) return run_block_mode(g, bs.data() + done, nb - done, st);
-    CKS(alloc_slot(g));
-    for (int i = done; i < nb; ++i) CKS(run_batch(g, bs[i], st));
+    int small_sched = sched == GBBC_SCHEDULE_AUTO ? g->tuned_schedule : sched;
+    size_t done = 0;
+    if (!small.empty() && small_sched == 0) {
+        if (small.size() >= 2) {
+            CKS(alloc_slot(g));
+            CK(g, cudaStreamSynchronize(st));
+            double t0 = now_s();
+            CKS(run_batch(g, small[0], st));
+            CK(g, cudaStreamSynchronize(st));
+            double t_grid = now_s() - t0;
+            int nblk = (int)std::min<size_t>(small.size() - 1, (size_t)g->nsm);
+            t0 = now_s();
+            CKS(run_block_mode(g, small.data() + 1, nblk, st));
+            double t_block = (now_s() - t0) / nblk;
+            done = 1 + (size_t)nblk;
+            g->tuned_schedule = t_block < t_grid ? GBBC_SCHEDULE_BLOCK : GBBC_SCHEDULE_GRID;
+            small_sched = g->tuned_schedule;
+        } else {
+            small_sched = GBBC_SCHEDULE_BLOCK;
+        }
+    }
+    if (small_sched == GBBC_SCHEDULE_BLOCK) {
+        CKS(run_block_mode(g, small.data() + done, (int)(small.size() - done), st));
+    } else {
+        CKS(alloc_slot(g));
+        for (size_t i = done; i < small.size(); ++i) CKS(run_batch(g, small[i], st));
+    }
+    if (!large.empty()) {
+        CKS(alloc_slot(g));
+        for (const BatchDesc& b : large) CKS(run_batch(g, b, st));
+    }
+    g->stats.schedule = large.empty() ? small_sched : (small.empty() ? GBBC_SCHEDULE_GRID : GBBC_SCHEDULE_AUTO);
     return GBBC_OK;
 }
 

@@ -114,10 +114,11 @@ struct Csr {
 };
 
 // ---- block-per-batch mode ----
-// One thread block runs a whole batch (forward and backward) with block
-// barriers only; blocks take batches from a work list.  Slot k holds the
-// state of the batch that block k is running, indexed by vertex - lo of the
-// batch's graph, so slots are sized for the largest graph of the handle.
+// One thread-block cluster (csize CTAs, csize = 1 is a single block) runs a
+// whole batch, forward and backward, separated by cluster barriers only;
+// clusters take batches from a work list.  Slot k holds the state of the
+// batch that cluster k is running, indexed by vertex - lo of the batch's
+// graph, so slots are sized for the largest graph of the handle.
 constexpr int kBlockThreads = 512;
 
 struct BlockBatch {
@@ -128,7 +129,10 @@ struct BlockBatch {
 struct BlockSlots {
     long long nslot = 0;  // vertices per slot
     long long qcap = 0;   // queue entries per slot
-    int count = 0;        // slots (= blocks of the launch)
+    int count = 0;        // slots (= clusters of the launch)
+    int csize = 1;        // thread blocks per cluster (per batch)
+    int* slot_batch = nullptr;  // [count] batch each slot is running
+    void* lsp = nullptr;  // [slot][nslot + 2] per-level "thread-per-entry" flags
     u64* vis = nullptr;
     u64* nx = nullptr;
     u64* ovf = nullptr;

@@ -1074,19 +1074,149 @@ __device__ __forceinline__ Slot slot_view(const BlockSlots& S, int k, int32_t lo
 template <typename T>
 __device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
 
-// One batch by the whole block.  Returns false when a count reached 2^64 in
-// the narrow format (the caller reruns the batch wide); BC is untouched then.
+// The CTAs of a thread-block cluster run one batch together.  The cluster
+// barrier (hardware, release/acquire at cluster scope) separates the steps;
+// a launch without clusters is a cluster of one CTA.
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void csync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// ---- thread-per-entry steps (sparse levels: few lanes per vertex, low degree)
+constexpr int kSparseBuf = 8;
+
+__device__ __forceinline__ void push_entry_thread(const Csr& g, const Slot& s, long long e, bool valid,
+                                                  StepStats& st) {
+    int32_t buf[kSparseBuf];
+    int cnt = 0;
+    if (valid) {
+        int32_t v = s.qv[e];
+        u64 m = s.qm[e];
+        for (int32_t p = __ldg(g.row_ptr + v), end = __ldg(g.row_ptr + v + 1); p < end; ++p) {
+            int32_t w = __ldg(g.col + p);
+            u64 nm = m & ~s.vis[w];
+            if (!nm) continue;
+            u64 old = atomicOr(&s.nx[w], nm);
+            st.lanes |= nm;
+            if (old != 0ull) continue;
+            st.esum += (unsigned long long)(__ldg(g.row_ptr + w + 1) - __ldg(g.row_ptr + w));
+            if (cnt < kSparseBuf) {
+                buf[cnt++] = w;
+            } else {  // rare: a long row; append alone
+                unsigned long long pos = atomicAdd(&s.ctr->qtail, 1ull);
+                if ((long long)pos < s.qcap) s.qv[pos] = w;
+                else atomicOr(&s.ctr->err, 1u);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kSparseBuf; ++i) warp_append(i < cnt, i < cnt ? buf[i] : 0, &s.ctr->qtail, s.qv, s.qcap,
+                                                      &s.ctr->err, 1u);
+}
+
 template <bool WIDE>
-__device__ bool block_batch(const Csr& g, const Slot& s, long long* lev, const BlockBatch& bb, const int32_t* src,
-                            u64* bc, int policy, const __half* wts, float max_deg, BwdWarpSmem& sm, int* sh,
-                            unsigned long long* stats) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+__device__ __forceinline__ void gather_entry_thread(const Csr& g, const Slot& s, const MaskTag* F, MaskTag* Fn,
+                                                    int level, long long e, unsigned long long& lsum) {
+    int32_t w = s.qv[e];
+    u64 m = s.nx[w];
+    s.qm[e] = m;
+    s.nx[w] = 0ull;
+    s.vis[w] |= m;
+    MaskTag tw;
+    tw.mask = m;
+    tw.tag = level + 1;
+    tw.pad = 0;
+    Fn[w] = tw;
+    lsum += (unsigned)__popcll(m);
+    const int32_t beg = __ldg(g.row_ptr + w), end = __ldg(g.row_ptr + w + 1);
+    u64 ovf_bits = 0ull;
+    for (u64 mm = m; mm; mm &= mm - 1) {
+        const int j = __ffsll((long long)mm) - 1;
+        u64 a = 0ull;
+        unsigned c = 0u;
+        WideAcc wa;
+        wa.a.lo = wa.a.hi = 0ull;
+        wa.x = INT_MIN;
+        wa.ovf = false;
+        for (int32_t p = beg; p < end; ++p) {
+            int32_t v = __ldg(g.col + p);
+            MaskTag t = F[v];
+            if (t.tag != level || !((t.mask >> j) & 1ull)) continue;
+            u64 x = ldv<false>(s.sigma + (size_t)v * kLanes + j);
+            a += x;
+            c |= a < x;
+            if (WIDE) pred_term<true>(s, v, j, x, s.ovf[v], wa);
+        }
+        s.sigma[(size_t)w * kLanes + j] = a;
+        if (c || (WIDE && wa.ovf)) {
+            ovf_bits |= 1ull << j;
+            if (WIDE) wide_store<true>(s, w, j, wa);
+        }
+    }
+    if (ovf_bits) {
+        s.ovf[w] |= ovf_bits;
+        atomicOr(&s.ctr->carry, 1u);
+    }
+}
+
+template <bool WIDE>
+__device__ __forceinline__ void bwd_entry_thread(const Csr& g, const Slot& s, const MaskTag* Fs, MaskTag* Fo,
+                                                 int level, long long e, u64* bc) {
+    int32_t v = s.qv[e];
+    u64 m = s.qm[e];
+    MaskTag tv;
+    tv.mask = m;
+    tv.tag = level;
+    tv.pad = 0;
+    Fo[v] = tv;
+    const int32_t beg = __ldg(g.row_ptr + v), end = __ldg(g.row_ptr + v + 1);
+    const u64 ov = WIDE ? s.ovf[v] : 0ull;
+    u128 total = {0ull, 0ull};
+    for (u64 mm = m; mm; mm &= mm - 1) {
+        const int j = __ffsll((long long)mm) - 1;
+        u64 N;
+        int E;
+        sigma_norm<WIDE>(s, v, j, ov, N, E);
+        u128 A = {0ull, 0ull};
+        for (int32_t p = beg; p < end; ++p) {
+            int32_t w = __ldg(g.col + p);
+            MaskTag t = Fs[w];
+            if (t.tag != level + 1 || !((t.mask >> j) & 1ull)) continue;
+            size_t at = (size_t)w * kLanes + j;
+            A = add128(A, psi_term<WIDE>(ldv<false>(s.psi + at), WIDE ? ldi<false>(s.psi_e + at) : 0, E));
+        }
+        total = add128(total, bwd_lane<WIDE>(s, v, j, N, E, A));
+    }
+    atomic_add128(bc + 2 * (size_t)v, total);
+}
+
+// One batch by the whole cluster (csize CTAs).  Returns false when a count
+// reached 2^64 in the narrow format (the caller reruns the batch wide); BC is
+// untouched then.  lsp[l] records whether level l ran thread-per-entry.
+template <bool WIDE>
+__device__ bool block_batch(const Csr& g, const Slot& s, long long* lev, unsigned char* lsp, const BlockBatch& bb,
+                            const int32_t* src, u64* bc, int policy, const __half* wts, float max_deg,
+                            BwdWarpSmem& sm, int* sh, unsigned long long* stats) {
+    const unsigned rank = cluster_rank(), csize = cluster_size();
+    const int tid = threadIdx.x, lane = tid & 31;
+    const long long ctid = (long long)rank * blockDim.x + tid, cthreads = (long long)csize * blockDim.x;
+    const int cwid = (int)(ctid >> 5), cnw = (int)(cthreads >> 5);
+    const bool lead = rank == 0;
     const int32_t lo = bb.lo, hi = bb.hi;
     const int nsrc = bb.nsrc;
     const float n_range = (float)(hi - lo);
     const float nnz_range = (float)(__ldg(g.row_ptr + hi) - __ldg(g.row_ptr + lo));
     // ---- clear the slot's range and counters ----
-    for (int32_t v = lo + tid; v < hi; v += blockDim.x) {
+    for (long long v = lo + ctid; v < hi; v += cthreads) {
         s.vis[v] = 0ull;
         s.nx[v] = 0ull;
         s.ovf[v] = 0ull;
@@ -1097,77 +1227,81 @@ __device__ bool block_batch(const Csr& g, const Slot& s, long long* lev, const B
         s.F[v] = t;
         s.F[s.n + v] = t;
     }
-    if (tid < (int)(sizeof(Counters) / sizeof(unsigned))) ((unsigned*)s.ctr)[tid] = 0u;
-    if (tid < kLanes) sh[tid] = tid < nsrc ? src[tid] : -1;
-    __syncthreads();
-    // ---- seed: distinct sources form the level-0 queue (first-occurrence order) ----
-    u64 mask = 0ull;
-    bool fj = false;
-    if (tid < nsrc) {
-        fj = true;
-        for (int i = 0; i < nsrc; ++i)
-            if (sh[i] == sh[tid]) {
-                mask |= 1ull << i;
-                if (i < tid) fj = false;
-            }
-        sh[kLanes + tid] = fj ? 1 : 0;
-    }
-    __syncthreads();
-    if (tid < nsrc) {
-        int32_t v = sh[tid];
-        atomicOr(&s.vis[v], 1ull << tid);
-        s.sigma[(size_t)v * kLanes + tid] = 1ull;
-        if (fj) {
-            int pos = 0;
-            for (int i = 0; i < tid; ++i) pos += sh[kLanes + i];
-            s.qv[pos] = v;
-            s.qm[pos] = mask;
-            MaskTag t;
-            t.mask = mask;
-            t.tag = 0;
-            t.pad = 0;
-            s.F[v] = t;
-            atomicAdd(&s.ctr->qtail, 1ull);
-            atomicAdd(&s.ctr->edge_sum, (unsigned long long)(__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v)));
+    if (lead && tid < (int)(sizeof(Counters) / sizeof(unsigned))) ((unsigned*)s.ctr)[tid] = 0u;
+    if (lead && tid < kLanes) sh[tid] = tid < nsrc ? src[tid] : -1;
+    csync();
+    // ---- seed (leading CTA): distinct sources form the level-0 queue ----
+    if (lead) {
+        u64 mask = 0ull;
+        bool fj = false;
+        if (tid < nsrc) {
+            fj = true;
+            for (int i = 0; i < nsrc; ++i)
+                if (sh[i] == sh[tid]) {
+                    mask |= 1ull << i;
+                    if (i < tid) fj = false;
+                }
+            sh[kLanes + tid] = fj ? 1 : 0;
         }
+        __syncthreads();
+        if (tid < nsrc) {
+            int32_t v = sh[tid];
+            atomicOr(&s.vis[v], 1ull << tid);
+            s.sigma[(size_t)v * kLanes + tid] = 1ull;
+            if (fj) {
+                int pos = 0;
+                for (int i = 0; i < tid; ++i) pos += sh[kLanes + i];
+                s.qv[pos] = v;
+                s.qm[pos] = mask;
+                MaskTag t;
+                t.mask = mask;
+                t.tag = 0;
+                t.pad = 0;
+                s.F[v] = t;
+                atomicAdd(&s.ctr->qtail, 1ull);
+                atomicAdd(&s.ctr->edge_sum,
+                          (unsigned long long)(__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v)));
+            }
+        }
+        if (tid == 0) {
+            s.ctr->lane_sum = (unsigned long long)nsrc;
+            s.ctr->lanes = nsrc == 64 ? ~0ull : ((1ull << nsrc) - 1ull);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            lev[0] = 0;
+            lev[1] = (long long)ld_cg(&s.ctr->qtail);
+        }
+        if (tid < 32) decide_step(s.ctr, 0, 0, policy, wts, n_range, nnz_range, max_deg);
     }
-    if (tid == 0) {
-        s.ctr->lane_sum = (unsigned long long)nsrc;
-        s.ctr->lanes = nsrc == 64 ? ~0ull : ((1ull << nsrc) - 1ull);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        lev[0] = 0;
-        lev[1] = (long long)ld_cg(&s.ctr->qtail);
-    }
-    if (wid == 0) decide_step(s.ctr, 0, 0, policy, wts, n_range, nnz_range, max_deg);
-    __syncthreads();
+    csync();
     // ---- forward, level by level ----
     int level = 0;
     unsigned long long npull = 0;
     for (;;) {
         const long long q_lo = ld_cg(lev + level), q_hi = ld_cg(lev + level + 1);
-        const int dir = ld_cg(&s.ctr->dir);
+        // a bottom-up step sweeps the whole range with this cluster alone:
+        // take it only when the range is not much larger than the frontier's
+        // edges (the policy's costs were measured on the whole GPU)
+        const int dir = ld_cg(&s.ctr->dir) && (double)n_range < 4.0 * (double)ld_cg(&s.ctr->edge_sum);
         const u64 lanes = ld_cg(&s.ctr->lanes);
-        __syncthreads();
-        if (tid == 0) {
+        // sparse level: few lanes per entry and short rows
+        const unsigned long long ents = (unsigned long long)(q_hi - q_lo);
+        const bool sparse = ld_cg(&s.ctr->lane_sum) <= 3ull * ents && ld_cg(&s.ctr->edge_sum) <= 16ull * ents;
+        csync();
+        if (lead && tid == 0) {
+            lsp[level] = sparse ? 1 : 0;
             s.ctr->heavy = s.ctr->tasks = s.ctr->medium = 0ull;
             s.ctr->edge_sum = s.ctr->scanned = 0ull;
             s.ctr->lanes = 0ull;
         }
-        __syncthreads();
+        csync();
         StepStats stats = {0ull, 0ull, 0ull};
-        if (!dir) {
-            for (long long e = q_lo + wid; e < q_hi; e += nw) {
-                int32_t v = s.qv[e];
-                u64 m = s.qm[e];
-                push_row(g, s, m, __ldg(g.row_ptr + v), __ldg(g.row_ptr + v + 1), lane, kWarp, stats);
-            }
-        } else {
+        if (dir) {
             ++npull;
             const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
-            for (long long base = lo; base < hi; base += blockDim.x) {
-                int32_t w = (int32_t)(base + tid);
+            for (long long base = lo + (ctid & ~31ll); base < hi; base += cthreads) {
+                int32_t w = (int32_t)(base + lane);
                 u64 u = w < hi ? (~s.vis[w] & lanes) : 0ull;
                 u64 f = 0ull;
                 int32_t beg = 0, end = 0;
@@ -1191,81 +1325,111 @@ __device__ bool block_batch(const Csr& g, const Slot& s, long long* lev, const B
                 }
                 warp_append(nm != 0ull, w, &s.ctr->qtail, s.qv, s.qcap, &s.ctr->err, 1u);
             }
+        } else if (sparse) {
+            for (long long base = q_lo + (ctid & ~31ll); base < q_hi; base += cthreads) {
+                long long e = base + lane;
+                push_entry_thread(g, s, e, e < q_hi, stats);
+            }
+        } else {
+            for (long long e = q_lo + cwid; e < q_hi; e += cnw) {
+                int32_t v = s.qv[e];
+                u64 m = s.qm[e];
+                push_row(g, s, m, __ldg(g.row_ptr + v), __ldg(g.row_ptr + v + 1), lane, kWarp, stats);
+            }
         }
         flush_stats(s, stats);
-        __syncthreads();
+        csync();
         const long long new_hi = (long long)ld_cg(&s.ctr->qtail);
         if (new_hi == q_hi || ld_cg(&s.ctr->err)) break;
-        if (tid == 0) {
+        // the new level's lane counts come from its own gather: judge it by
+        // the current level's lanes and the new level's degrees
+        const unsigned long long nents = (unsigned long long)(new_hi - q_hi);
+        const bool gsparse = sparse && ld_cg(&s.ctr->edge_sum) <= 16ull * nents;
+        csync();
+        if (lead && tid == 0) {
             s.ctr->lane_sum = s.ctr->lane_esum = 0ull;
             lev[level + 2] = new_hi;
         }
-        __syncthreads();
+        csync();
         // ---- gather of level+1 (finalize masks, sigma sums) ----
         {
             const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
             MaskTag* Fn = s.F + (size_t)((level + 1) & 1) * s.n;
             unsigned long long lsum = 0;
-            for (long long e = q_hi + wid; e < new_hi; e += nw) {
-                int32_t w = s.qv[e];
-                u64 m = s.nx[w];
-                int32_t beg = __ldg(g.row_ptr + w), end = __ldg(g.row_ptr + w + 1);
-                __syncwarp();
-                if (lane == 0) {
-                    s.qm[e] = m;
-                    s.nx[w] = 0ull;
-                    s.vis[w] |= m;
-                    MaskTag t;
-                    t.mask = m;
-                    t.tag = level + 1;
-                    t.pad = 0;
-                    Fn[w] = t;
-                    lsum += (unsigned)__popcll(m);
+            if (gsparse) {
+                for (long long e = q_hi + ctid; e < new_hi; e += cthreads)
+                    gather_entry_thread<WIDE>(g, s, F, Fn, level, e, lsum);
+                for (int o = 16; o >= 1; o >>= 1) lsum += __shfl_xor_sync(FULL, lsum, o);
+            } else {
+                for (long long e = q_hi + cwid; e < new_hi; e += cnw) {
+                    int32_t w = s.qv[e];
+                    u64 m = s.nx[w];
+                    int32_t beg = __ldg(g.row_ptr + w), end = __ldg(g.row_ptr + w + 1);
+                    __syncwarp();
+                    if (lane == 0) {
+                        s.qm[e] = m;
+                        s.nx[w] = 0ull;
+                        s.vis[w] |= m;
+                        MaskTag t;
+                        t.mask = m;
+                        t.tag = level + 1;
+                        t.pad = 0;
+                        Fn[w] = t;
+                        lsum += (unsigned)__popcll(m);
+                    }
+                    GatherAcc acc;
+                    gather_init(acc);
+                    fwd_gather_row<1, WIDE, false>(g, s, F, level, m, beg, end, 0, acc);
+                    fwd_store<WIDE>(s, w, m, acc);
                 }
-                GatherAcc acc;
-                gather_init(acc);
-                fwd_gather_row<1, WIDE, false>(g, s, F, level, m, beg, end, 0, acc);
-                fwd_store<WIDE>(s, w, m, acc);
             }
             if (lane == 0 && lsum) atomicAdd(&s.ctr->lane_sum, lsum);
         }
-        __syncthreads();
-        if (wid == 0) decide_step(s.ctr, q_hi, level + 1, policy, wts, n_range, nnz_range, max_deg);
-        __syncthreads();
+        csync();
+        if (lead && tid < 32) decide_step(s.ctr, q_hi, level + 1, policy, wts, n_range, nnz_range, max_deg);
+        csync();
         ++level;
     }
     const int nlev = level + 1;
-    if (tid == 0) {
+    if (lead && tid == 0) {
         atomicAdd(stats + 1, (unsigned long long)nlev);
         atomicAdd(stats + 2, npull);
+        lsp[nlev] = 1;
     }
     if (ld_cg(&s.ctr->err)) return true;  // reported by the host; BC is not trusted
     if (!WIDE && ld_cg(&s.ctr->carry)) return false;
+    csync();
     // ---- backward, levels nlev-1 .. 1 ----
     for (int l = nlev - 1; l >= 1; --l) {
         const long long q_lo = ld_cg(lev + l), q_hi = ld_cg(lev + l + 1);
         const MaskTag* Fs = s.F + (size_t)((l + 1) & 1) * s.n;
         MaskTag* Fo = s.F + (size_t)(l & 1) * s.n;
-        for (long long e = q_lo + wid; e < q_hi; e += nw) {
-            int32_t v = s.qv[e];
-            u64 m = s.qm[e];
-            if (lane == 0) {
-                MaskTag t;
-                t.mask = m;
-                t.tag = l;
-                t.pad = 0;
-                Fo[v] = t;
+        const bool sp = ld_cg(lsp + l) != 0;
+        if (sp) {
+            for (long long e = q_lo + ctid; e < q_hi; e += cthreads) bwd_entry_thread<WIDE>(g, s, Fs, Fo, l, e, bc);
+        } else {
+            for (long long e = q_lo + cwid; e < q_hi; e += cnw) {
+                int32_t v = s.qv[e];
+                u64 m = s.qm[e];
+                if (lane == 0) {
+                    MaskTag t;
+                    t.mask = m;
+                    t.tag = l;
+                    t.pad = 0;
+                    Fo[v] = t;
+                }
+                u64 N0, N1;
+                int E0, E1;
+                lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
+                u128 a0, a1;
+                bwd_row_begin(sm, E0, E1);
+                bwd_gather_row<1, WIDE, false>(g, s, Fs, l, m, __ldg(g.row_ptr + v), __ldg(g.row_ptr + v + 1), 0,
+                                               sm);
+                bwd_row_end(sm, a0, a1);
+                bwd_store<WIDE, true>(s, bc, v, m, E0, E1, N0, N1, a0, a1);
             }
-            u64 N0, N1;
-            int E0, E1;
-            lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
-            u128 a0, a1;
-            bwd_row_begin(sm, E0, E1);
-            bwd_gather_row<1, WIDE, false>(g, s, Fs, l, m, __ldg(g.row_ptr + v), __ldg(g.row_ptr + v + 1), 0, sm);
-            bwd_row_end(sm, a0, a1);
-            bwd_store<WIDE, true>(s, bc, v, m, E0, E1, N0, N1, a0, a1);
         }
-        __syncthreads();
+        csync();
     }
     return true;
 }
@@ -1274,29 +1438,34 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_batches(Csr g, BlockSlo
                                                                  int nb, const int32_t* srcs, unsigned* next,
                                                                  u64* bc, int policy, const __half* wts,
                                                                  const long long* gmaxdeg,
-                                                                 unsigned long long* stats, int start_wide) {
+                                                                 unsigned long long* stats, int start_wide,
+                                                                 int* slot_batch) {
     extern __shared__ unsigned char dsm[];
     BwdWarpSmem* smem = reinterpret_cast<BwdWarpSmem*>(dsm);
     BwdWarpSmem& sm = smem[threadIdx.x >> 5];
-    __shared__ int sh[2 * kLanes + 1];
+    __shared__ int sh[2 * kLanes];
     bwd_smem_zero(sm);
-    long long* lev = S.lev + (long long)blockIdx.x * (S.nslot + 2);
+    const unsigned rank = cluster_rank();
+    const int slot = blockIdx.x / (int)cluster_size();
+    long long* lev = S.lev + (long long)slot * (S.nslot + 2);
+    unsigned char* lsp = reinterpret_cast<unsigned char*>(S.lsp) + (long long)slot * (S.nslot + 2);
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) sh[2 * kLanes] = (int)atomicAdd(next, 1u);
-        __syncthreads();
-        const int b = sh[2 * kLanes];
+        if (rank == 0 && threadIdx.x == 0) slot_batch[slot] = (int)atomicAdd(next, 1u);
+        csync();
+        const int b = ld_cg(slot_batch + slot);
+        csync();
         if (b >= nb) break;
         const BlockBatch bb = batches[b];
-        const Slot v = slot_view(S, blockIdx.x, bb.lo);
+        const Slot v = slot_view(S, slot, bb.lo);
         const float md = (float)gmaxdeg[bb.gi];
-        __syncthreads();
-        if (start_wide || !block_batch<false>(g, v, lev, bb, srcs + bb.src_off, bc, policy, wts, md, sm, sh, stats)) {
-            __syncthreads();
-            if (threadIdx.x == 0 && !start_wide) atomicAdd(stats + 3, 1ull);
-            block_batch<true>(g, v, lev, bb, srcs + bb.src_off, bc, policy, wts, md, sm, sh, stats);
+        if (start_wide || !block_batch<false>(g, v, lev, lsp, bb, srcs + bb.src_off, bc, policy, wts, md, sm, sh,
+                                              stats)) {
+            csync();
+            if (rank == 0 && threadIdx.x == 0 && !start_wide) atomicAdd(stats + 3, 1ull);
+            block_batch<true>(g, v, lev, lsp, bb, srcs + bb.src_off, bc, policy, wts, md, sm, sh, stats);
         }
-        if (threadIdx.x == 0) atomicAdd(stats, 1ull);
+        if (rank == 0 && threadIdx.x == 0) atomicAdd(stats, 1ull);
+        csync();
     }
 }
 
@@ -1307,10 +1476,25 @@ cudaError_t launch_block_batches(const Csr& g, const BlockSlots& S, const BlockB
     const size_t smem = (size_t)(kBlockThreads / kWarp) * sizeof(BwdWarpSmem);
     cudaError_t e = cudaFuncSetAttribute(k_block_batches, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_block_batches<<<S.count, kBlockThreads, smem, st>>>(g, S, batches, nb, srcs, next, bc, policy,
-                                                          (const __half*)weights_fp16, graph_max_deg, stats,
-                                                          start_wide ? 1 : 0);
-    return cudaGetLastError();
+    if (S.csize > 8) {
+        e = cudaFuncSetAttribute(k_block_batches, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(S.count * S.csize), 1, 1);
+    cfg.blockDim = dim3(kBlockThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)S.csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int start = start_wide ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_block_batches, g, S, batches, nb, srcs, next, bc, policy,
+                              (const __half*)weights_fp16, graph_max_deg, stats, start, S.slot_batch);
 }
 
 // ---------------------------------------------------------------------------

@@ -40,7 +40,7 @@ def training_graphs(seed=0):
     out = []
     for s in (14, 15, 16, 17):
         out.append((f"rmat{s}", gg.rmat(s, 16, seed=seed + 100 + s)))
-    for side in (96, 160, 256):
+    for side in (96, 160, 256, 512, 1024):
         out.append((f"grid{side}", gg.grid(side, "0.05", seed=seed + 200 + side)))
     return out
 
@@ -51,10 +51,11 @@ def collect(graphs, sources=256, width=64, policy="beamer", seed=1):
     from . import graphgen as gg
     recs = []
     for name, g in graphs:
-        S = gg.sample_sources(g.n, min(sources, g.n), seed=seed)
+        # large high-diameter graphs: one batch is thousands of levels
+        S = gg.sample_sources(g.n, min(sources if g.n < 200000 else 64, g.n), seed=seed)
         flags = gbbc.GBBC_TRACE | gbbc.GBBC_TRACE_BOTH
         with gbbc.BC.from_graph(g, batch_width=width, policy=policy, flags=flags) as bc:
-            bc.compute(S[:64])  # warm-up (not kept)
+            bc.compute(S[:min(64, len(S), 8 if g.n >= 200000 else 64)])  # warm-up (not kept)
             bc.clear_trace()
             bc.compute(S)
             tr = bc.trace()
