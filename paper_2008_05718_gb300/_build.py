@@ -19,6 +19,9 @@ LIB = os.path.join(HERE, "libgbbc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr"] + ARCH
+# extra nvcc flags (e.g. -D tuning macros), also part of the staleness check
+EXTRA = os.environ.get("GBBC_NVCC_FLAGS", "").split()
+STAMP = os.path.join(BUILD, "flags.txt")
 
 
 def nvcc() -> str:
@@ -39,6 +42,8 @@ def headers():
 def stale() -> bool:
     if not os.path.exists(LIB):
         return True
+    if (open(STAMP).read() if os.path.exists(STAMP) else "") != " ".join(EXTRA):
+        return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(p) > t for p in sources() + headers())
 
@@ -52,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [cc, *NVCC_FLAGS, "-c", src, "-o", obj]
+        cmd = [cc, *NVCC_FLAGS, *EXTRA, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd))
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -68,6 +73,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.check_call([cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(EXTRA))
     return LIB
 
 

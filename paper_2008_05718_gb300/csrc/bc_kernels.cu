@@ -451,14 +451,27 @@ __device__ __forceinline__ void pred_term(const Slot& s, int32_t v, int lane_id,
 // Up to four contributing neighbours per round: their (vertex, mask) pairs
 // are broadcast from the ballot, then all loads are issued before any is
 // used, so a warp keeps several independent loads in flight.
-struct Round4 {
-    int32_t v[4];
-    u64 f[4];
-};
+#ifndef GBBC_GATHER_ROUND
+#define GBBC_GATHER_ROUND 4
+#endif
+#ifndef GBBC_GATHER_MIN_BLOCKS
+#define GBBC_GATHER_MIN_BLOCKS 1
+#endif
+#ifndef GBBC_BWD_MIN_BLOCKS
+#define GBBC_BWD_MIN_BLOCKS 1
+#endif
 
-__device__ __forceinline__ void take_round(unsigned& bal, int32_t v, u64 f, Round4& r) {
+template <int R>
+struct RoundR {
+    int32_t v[R];
+    u64 f[R];
+};
+typedef RoundR<4> Round4;
+
+template <int R>
+__device__ __forceinline__ void take_round(unsigned& bal, int32_t v, u64 f, RoundR<R>& r) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < R; ++u) {
         int src = bal ? __ffs(bal) - 1 : -1;
         if (bal) bal &= bal - 1;
         int sl = src < 0 ? 0 : src;
@@ -506,17 +519,18 @@ __device__ __forceinline__ void fwd_gather_row(const Csr& g, const Slot& s, cons
             }
         } else {
             while (bal) {
-                Round4 r;
-                take_round(bal, v, f, r);
-                u64 x0[4], x1[4];
+                constexpr int R = GBBC_GATHER_ROUND;
+                RoundR<R> r;
+                take_round<R>(bal, v, f, r);
+                u64 x0[R], x1[R];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < R; ++u) {
                     const u64* row = s.sigma + (size_t)r.v[u] * kLanes;
                     x0[u] = ((r.f[u] >> lane) & 1ull) ? ldv<NC>(row + lane) : 0ull;
                     x1[u] = ((r.f[u] >> (lane + 32)) & 1ull) ? ldv<NC>(row + lane + 32) : 0ull;
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < R; ++u) {
                     acc.a0 += x0[u];
                     acc.c0 |= acc.a0 < x0[u];
                     acc.a1 += x1[u];
@@ -561,7 +575,8 @@ __device__ __forceinline__ void fwd_store(const Slot& s, int32_t w, u64 m, const
 }
 
 template <bool WIDE>
-__global__ void k_fwd_gather(Csr g, Slot s, long long q_lo, int level, int heavy_deg) {
+__global__ void __launch_bounds__(kBlock, GBBC_GATHER_MIN_BLOCKS) k_fwd_gather(Csr g, Slot s, long long q_lo,
+                                                                             int level, int heavy_deg) {
     const int lane = threadIdx.x & 31;
     const long long q_hi = (long long)s.ctr->qtail;  // end of the entries the discovery queued
     const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
@@ -799,7 +814,7 @@ __device__ __forceinline__ void bwd_gather_row(const Csr& g, const Slot& s, cons
         unsigned bal = __ballot_sync(FULL, f != 0);
         while (bal) {
             Round4 r;
-            take_round(bal, w, f, r);
+            take_round<4>(bal, w, f, r);
             int K = 0;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -926,7 +941,8 @@ __device__ __forceinline__ void lane_norms(const Slot& s, int32_t v, u64 m, u64&
 }
 
 template <bool WIDE>
-__global__ void __launch_bounds__(kBlock) k_bwd(Csr g, Slot s, u64* bc, long long q_lo, long long q_hi, int level,
+__global__ void __launch_bounds__(kBlock, GBBC_BWD_MIN_BLOCKS) k_bwd(Csr g, Slot s, u64* bc, long long q_lo,
+                                                                     long long q_hi, int level,
                                                int heavy_deg) {
     const int lane = threadIdx.x & 31;
     __shared__ BwdWarpSmem smem[kBlock / kWarp];

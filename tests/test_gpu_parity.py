@@ -346,3 +346,30 @@ def test_fixed_point_partials_add_to_identical_bits(gb):
     total = mr.sum_fixed(parts)
     assert np.array_equal(total, whole_fixed)
     assert np.array_equal(mr.fixed_to_double(total), whole)
+
+
+# ---- the remaining workloads at full size (sampled sources) ------------------
+
+def test_multi_workload_full_size_sampled(gb):
+    # the 256-graph mix in one handle; two sources per graph, checked graph by graph
+    mw = gg.multi_workload()
+    assert len(mw.graphs) == 256
+    gids, locs, per = [], [], []
+    for i, (g, S) in enumerate(zip(mw.graphs, mw.sources)):
+        sel = S[:2]
+        per.append(sel)
+        gids += [i] * len(sel)
+        locs += list(sel)
+    with gb.BC.from_graphs(mw.graphs) as bc:
+        bc.compute_multi(np.array(gids, np.int32), np.array(locs, np.int32))
+        st = bc.stats()
+        for i in range(0, 256, 15):
+            want, _ = oracle.bc_graph(mw.graphs[i], per[i])
+            assert_bc_close(bc.read(graph_id=i), want)
+    assert st["batches"] == 256 and st["wide_batches"] > 0
+
+
+def test_rmat22_full_size_sampled(gb):
+    # the largest workload (4.2M vertices, ~128M entries): one batch of 8 sources
+    g, S = gg.workload("rmat22")
+    check(gb, g, S[:8], keep=(0, 7), batch_width=64)
