@@ -454,11 +454,18 @@ __device__ __forceinline__ void pred_term(const Slot& s, int32_t v, int lane_id,
 #ifndef GBBC_GATHER_ROUND
 #define GBBC_GATHER_ROUND 4
 #endif
-#ifndef GBBC_GATHER_MIN_BLOCKS
-#define GBBC_GATHER_MIN_BLOCKS 1
+// Occupancy hints for tuning builds only: an explicit minimum of blocks per
+// SM changes ptxas's register allocation, and the defaults (none for the
+// gather, the block size alone for the backward) measured fastest.
+#ifdef GBBC_GATHER_MIN_BLOCKS
+#define GBBC_GATHER_BOUNDS __launch_bounds__(kBlock, GBBC_GATHER_MIN_BLOCKS)
+#else
+#define GBBC_GATHER_BOUNDS
 #endif
-#ifndef GBBC_BWD_MIN_BLOCKS
-#define GBBC_BWD_MIN_BLOCKS 1
+#ifdef GBBC_BWD_MIN_BLOCKS
+#define GBBC_BWD_BOUNDS __launch_bounds__(kBlock, GBBC_BWD_MIN_BLOCKS)
+#else
+#define GBBC_BWD_BOUNDS __launch_bounds__(kBlock)
 #endif
 
 template <int R>
@@ -575,8 +582,7 @@ __device__ __forceinline__ void fwd_store(const Slot& s, int32_t w, u64 m, const
 }
 
 template <bool WIDE>
-__global__ void __launch_bounds__(kBlock, GBBC_GATHER_MIN_BLOCKS) k_fwd_gather(Csr g, Slot s, long long q_lo,
-                                                                             int level, int heavy_deg) {
+__global__ void GBBC_GATHER_BOUNDS k_fwd_gather(Csr g, Slot s, long long q_lo, int level, int heavy_deg) {
     const int lane = threadIdx.x & 31;
     const long long q_hi = (long long)s.ctr->qtail;  // end of the entries the discovery queued
     const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
@@ -941,8 +947,7 @@ __device__ __forceinline__ void lane_norms(const Slot& s, int32_t v, u64 m, u64&
 }
 
 template <bool WIDE>
-__global__ void __launch_bounds__(kBlock, GBBC_BWD_MIN_BLOCKS) k_bwd(Csr g, Slot s, u64* bc, long long q_lo,
-                                                                     long long q_hi, int level,
+__global__ void GBBC_BWD_BOUNDS k_bwd(Csr g, Slot s, u64* bc, long long q_lo, long long q_hi, int level,
                                                int heavy_deg) {
     const int lane = threadIdx.x & 31;
     __shared__ BwdWarpSmem smem[kBlock / kWarp];
