@@ -91,11 +91,12 @@ typedef struct gbbc_options {
 
 /* How batches are mapped to the GPU. */
 enum gbbc_schedule {
-    GBBC_SCHEDULE_AUTO = 0,  /* batches of graphs above 65,536 vertices run
-                                grid; for the others the first call times its
-                                first batches in both modes (results kept) and
-                                the faster mode is kept for the handle; results
-                                are identical either way */
+    GBBC_SCHEDULE_AUTO = 0,  /* batches of graphs above 65,536 vertices with
+                                average degree above 6 run grid; for the others
+                                the first call times its first batches in both
+                                modes (results kept) and the faster mode is
+                                kept for the handle; results are identical
+                                either way */
     GBBC_SCHEDULE_GRID = 1,  /* one batch at a time on the whole GPU, a kernel
                                 per level step, host read-back per level */
     GBBC_SCHEDULE_BLOCK = 2  /* one thread-block cluster (1 to 8 blocks) per

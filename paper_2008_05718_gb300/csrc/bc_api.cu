@@ -840,13 +840,23 @@ double now_s() {
                std::chrono::steady_clock::now().time_since_epoch()).count() * 1e-9;
 }
 
-// Graphs above this many vertices always run in the grid schedule: one
-// block per batch cannot hide the latency of their wide levels.
+// Graphs above this many vertices with an average degree above
+// kBlockMaxAvgDegree run in the grid schedule: one cluster per batch cannot
+// hide the latency of their wide levels.  Sparse large graphs (road-like,
+// thousands of levels) run block: their cost is per level, not per edge.
 constexpr long long kBlockMaxVertices = 65536;
+constexpr double kBlockMaxAvgDegree = 6.0;
+
+bool grid_graph(const gbbc_graph* g, const BatchDesc& b) {
+    long long n = (long long)b.hi - b.lo;
+    if (n <= kBlockMaxVertices) return false;
+    double nnz = (double)g->h_row_ptr[b.hi] - (double)g->h_row_ptr[b.lo];
+    return nnz > kBlockMaxAvgDegree * (double)n;
+}
 
 // Grid or block for each batch: fixed by the options, forced to grid when
 // per-level state is kept or traced.  Under GBBC_SCHEDULE_AUTO, batches of
-// graphs above kBlockMaxVertices run grid; the others run block unless a
+// large dense graphs (grid_graph) run grid; the others run block unless a
 // timed trial (the call's first batches, whose results are kept: one in
 // grid, one wave in block) shows grid faster; the choice is kept per handle.
 gbbc_status dispatch(gbbc_graph* g, const std::vector<BatchDesc>& bs, cudaStream_t st) {
@@ -854,7 +864,7 @@ gbbc_status dispatch(gbbc_graph* g, const std::vector<BatchDesc>& bs, cudaStream
     if (g->k_dist || (g->opt.flags & GBBC_TRACE)) sched = GBBC_SCHEDULE_GRID;
     std::vector<BatchDesc> small, large;
     if (sched == GBBC_SCHEDULE_AUTO) {
-        for (const BatchDesc& b : bs) ((long long)b.hi - b.lo > kBlockMaxVertices ? large : small).push_back(b);
+        for (const BatchDesc& b : bs) (grid_graph(g, b) ? large : small).push_back(b);
     } else {
         (sched == GBBC_SCHEDULE_BLOCK ? small : large) = bs;
     }
