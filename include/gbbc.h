@@ -272,7 +272,7 @@ gbbc_status bc_get_profile(const gbbc_graph* g, gbbc_kernel_profile* out, int32_
  * are the six features of gbbc_level_trace.features.  The network only
  * chooses the schedule: BC, dist and sigma do not depend on it.  The paper
  * has no learned component; its nearest analogue is choosing the CPU:GPU
- * split from measured run times (Sec. V-C).
+ * split from measured run times (Sec. V-D).
  *
  * bc_mlp_* run on the device: params, x (n x 6, row-major), target, weight,
  * out, grad, loss pointers are DEVICE memory (FP32); they synchronize the

@@ -6,7 +6,7 @@ arithmetic.  The generators live in ``graphgen.c`` (plain C, integer-only
 SplitMix64 randomness, so the same seed gives the same bytes on x86-64 and
 AArch64); this wrapper compiles it on first use and returns numpy arrays.
 
-Graph families (shapes of the paper's workload classes, Table I of Sec. V):
+Graph families (shapes of the paper's workload classes, Table I of Sec. VI):
 Erdos-Renyi G(n, p), R-MAT scale-free graphs (social/web class), 4-neighbour
 grids with edges removed (road-network class: high diameter, degree <= 4),
 and small closed-form graphs (path, star, cycle, complete, complete

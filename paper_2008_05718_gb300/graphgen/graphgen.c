@@ -5,7 +5,7 @@
  * lists.  It holds none of the betweenness-centrality arithmetic, so both the
  * CUDA library and the CPU oracle may consume what it writes.
  *
- * Graph conventions (Sec. V, "directed graphs were converted to undirected"):
+ * Graph conventions (Sec. VI, "directed graphs were converted to undirected"):
  * every graph is returned symmetric, with no self-loops, no duplicate entries
  * and rows sorted ascending; row_ptr and col are int32 (nnz < 2^31).
  *
