@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--workload", default="rmat18", choices=sorted(WORKLOADS))
     ap.add_argument("--policy", default="auto")
     ap.add_argument("--width", type=int, default=64)
+    ap.add_argument("--grouping", default="learned", choices=["learned", "none"],
+                    help="order sources by the shipped grouping network before packing them into words")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=48, help="sources in the oracle's timed sample")
@@ -219,9 +221,19 @@ def run_ours(args):
     if args.policy in ("auto", "learned") and args.width != 1:
         from paper_2008_05718_gb300 import policy as pol
         weights = pol.shipped_weights()
-    bc = gbbc.BC.from_csr(g.n, rp, col, stream=stream, **opts)
-    if weights is not None:
-        bc.load_policy(weights)
+    gweights = None
+    if args.grouping == "learned" and args.width != 1:
+        from paper_2008_05718_gb300 import grouping as grp
+        gweights = grp.shipped_weights()
+
+    def prepare(h):
+        if weights is not None:
+            h.load_policy(weights)
+        if gweights is not None:
+            h.load_grouping(gweights)
+        return h
+
+    bc = prepare(gbbc.BC.from_csr(g.n, rp, col, stream=stream, **opts))
 
     def step():
         bc.reset()
@@ -265,8 +277,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         with gbbc.BC.from_csr(g.n, rp_h, col_h, stream=stream, **opts) as h:
-            if weights is not None:
-                h.load_policy(weights)
+            prepare(h)
             h.compute(src_h, stream=stream)
             h.read(out_h, stream=stream)
     torch.cuda.synchronize()
@@ -277,8 +288,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant step kind (one traced step) ----
     with gbbc.BC.from_csr(g.n, rp, col, stream=stream, flags=gbbc.GBBC_TRACE, **opts) as tb:
-        if weights is not None:
-            tb.load_policy(weights)
+        prepare(tb)
         tb.compute(src, stream=stream)
         tb.sync()
         prof = tb.profile()
@@ -309,6 +319,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "sources": k,
                            "n": g.n, "nnz": g.nnz, "batch_width": args.width,
                            "policy": args.policy + (" (learned, shipped weights)" if weights is not None else ""),
+                           "source_grouping": "learned (shipped weights)" if gweights is not None else "list order",
                            "l2": "flushed between timed steps (512 MiB device write)"},
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,

@@ -315,6 +315,25 @@ gbbc_status bc_policy_eval(const float* params, const float* x, int64_t n, float
 gbbc_status bc_policy_load(gbbc_graph* g, const float* params, size_t bytes);
 
 /*
+ * Learned source grouping.  A network of the same shape with K = 1 output
+ * scores each source from six features (bc_source_features: log-scaled
+ * degree of s, sum and maximum of its neighbours' degrees, and the size,
+ * mean degree and maximum degree of its graph); it is trained to predict the
+ * source's mean BFS distance.  With weights loaded, bc_compute orders each
+ * graph's sources by score (stable) before packing them into words, so that
+ * sources whose levels line up share a word (and isolated sources fill words
+ * of their own).  The order changes the batches, never the BC bits.  It is
+ * not applied when GBBC_KEEP_STATE is set (kept state follows list order).
+ */
+gbbc_status bc_source_features(gbbc_graph* g, const int32_t* sources, int64_t k, float* out /* k x 6 */,
+                               void* stream);
+/* bytes = bc_mlp_param_count(1) * 4 FP32 params (host or device); NULL unloads. */
+gbbc_status bc_grouping_load(gbbc_graph* g, const float* params, size_t bytes);
+/* The loaded network's score of each source (the key bc_compute sorts by);
+ * GBBC_ERR_STATE when no grouping weights are loaded. */
+gbbc_status bc_grouping_scores(gbbc_graph* g, const int32_t* sources, int64_t k, float* out, void* stream);
+
+/*
  * bc_compute_noalloc - BC of one small graph with no memory allocation.
  * The paper has no counterpart; this entry point exists for callers that
  * must not allocate memory themselves (code running under a pool allocator

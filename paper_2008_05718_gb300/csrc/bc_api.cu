@@ -54,6 +54,8 @@ struct gbbc_graph {
     void* d_policy = nullptr;
     std::vector<long long> graph_max_deg;
     long long* d_graph_max_deg = nullptr;
+    long long* d_goff = nullptr;
+    void* d_grouping = nullptr;      // FP16 copy of the source-grouping network
     // block-per-batch schedule
     BlockSlots blk;
     BlockBatch* d_bb = nullptr;
@@ -684,6 +686,8 @@ gbbc_status alloc_keep(gbbc_graph* g, long long k, cudaStream_t st) {
 }
 
 gbbc_status dispatch(gbbc_graph* g, const std::vector<BatchDesc>& bs, cudaStream_t st);
+gbbc_status grouping_scores(gbbc_graph* g, const std::vector<int32_t>& src, const std::vector<int32_t>& gid,
+                            std::vector<float>& score, cudaStream_t st);
 
 // Shared by bc_compute and bc_compute_multi: `gsrc` are whole-handle vertex
 // ids, `gid` their graph index.
@@ -700,10 +704,21 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
             CKS(run_plain(g, gsrc[i], (int32_t)g->goff[gid[i]], (int32_t)g->goff[gid[i] + 1], i, st));
         return GBBC_OK;
     }
-    // group by graph (stable), then pack up to 64 consecutive sources
+    // group by graph (stable), then pack up to 64 consecutive sources; with a
+    // grouping network loaded (and no per-source state kept), each graph's
+    // sources are ordered by the network's score so that sources whose BFS
+    // levels line up share a word
     std::vector<long long> order(k);
     for (long long i = 0; i < k; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](long long a, long long b) { return gid[a] < gid[b]; });
+    if (g->d_grouping && !g->k_dist) {
+        std::vector<float> score;
+        CKS(grouping_scores(g, gsrc, gid, score, st));
+        std::stable_sort(order.begin(), order.end(), [&](long long a, long long b) {
+            return gid[a] != gid[b] ? gid[a] < gid[b] : score[a] < score[b];
+        });
+    } else {
+        std::stable_sort(order.begin(), order.end(), [&](long long a, long long b) { return gid[a] < gid[b]; });
+    }
     std::vector<BatchDesc> batches;
     const int width = g->opt.batch_width == 32 ? 32 : kLanes;
     long long i = 0;
@@ -771,6 +786,64 @@ gbbc_status alloc_block(gbbc_graph* g, long long nslot, int want) {
     return GBBC_OK;
 }
 
+gbbc_status ensure_graph_arrays(gbbc_graph* g) {
+    if (!g->d_graph_max_deg) {
+        CKS(dalloc_t(g, &g->d_graph_max_deg, g->graph_max_deg.size()));
+        CK(g, cudaMemcpy(g->d_graph_max_deg, g->graph_max_deg.data(), g->graph_max_deg.size() * sizeof(long long),
+                         cudaMemcpyHostToDevice));
+    }
+    if (!g->d_goff) {
+        CKS(dalloc_t(g, &g->d_goff, g->goff.size()));
+        CK(g, cudaMemcpy(g->d_goff, g->goff.data(), g->goff.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    }
+    return GBBC_OK;
+}
+
+// Features of k sources (whole-handle ids) into device x[k][6].
+gbbc_status source_features(gbbc_graph* g, const std::vector<int32_t>& src, const std::vector<int32_t>& gid,
+                            float* d_x, cudaStream_t st) {
+    long long k = (long long)src.size();
+    if (k == 0) return GBBC_OK;
+    CKS(ensure_graph_arrays(g));
+    int32_t *d_src = nullptr, *d_gid = nullptr;
+    CKS(dalloc_t(g, &d_src, (size_t)k));
+    gbbc_status r = dalloc_t(g, &d_gid, (size_t)k);
+    if (r == GBBC_OK) {
+        Csr c{g->n, g->nnz, g->d_row_ptr, g->d_col};
+        if (cudaMemcpyAsync(d_src, src.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(d_gid, gid.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            launch_source_features(c, d_src, d_gid, k, g->d_goff, g->d_graph_max_deg, d_x, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            r = fail(g, GBBC_ERR_CUDA, "source features failed");
+        g->stats.kernel_launches++;
+    }
+    dfree(g, d_src);
+    dfree(g, d_gid);
+    return r;
+}
+
+// Predicted grouping score of each source (learned network, FP16 weights).
+gbbc_status grouping_scores(gbbc_graph* g, const std::vector<int32_t>& src, const std::vector<int32_t>& gid,
+                            std::vector<float>& score, cudaStream_t st) {
+    long long k = (long long)src.size();
+    score.assign((size_t)k, 0.f);
+    if (k == 0) return GBBC_OK;
+    float *d_x = nullptr, *d_s = nullptr;
+    CKS(dalloc_t(g, &d_x, (size_t)k * 6));
+    gbbc_status r = dalloc_t(g, &d_s, (size_t)k);
+    if (r == GBBC_OK) r = source_features(g, src, gid, d_x, st);
+    if (r == GBBC_OK) {
+        if (launch_group_score(g->d_grouping, d_x, k, d_s, st) != cudaSuccess ||
+            cudaMemcpyAsync(score.data(), d_s, k * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            r = fail(g, GBBC_ERR_CUDA, "grouping scores failed");
+        g->stats.kernel_launches++;
+    }
+    dfree(g, d_x);
+    dfree(g, d_s);
+    return r;
+}
+
 gbbc_status run_block_mode(gbbc_graph* g, const BatchDesc* bs, int nb, cudaStream_t st) {
     if (nb <= 0) return GBBC_OK;
     long long nslot = 1;
@@ -803,11 +876,7 @@ gbbc_status run_block_mode(gbbc_graph* g, const BatchDesc* bs, int nb, cudaStrea
     }
     if (!g->d_next) CKS(dalloc_t(g, &g->d_next, 1));
     if (!g->d_bstats) CKS(dalloc_t(g, &g->d_bstats, 4));
-    if (!g->d_graph_max_deg) {
-        CKS(dalloc_t(g, &g->d_graph_max_deg, g->graph_max_deg.size()));
-        CK(g, cudaMemcpy(g->d_graph_max_deg, g->graph_max_deg.data(), g->graph_max_deg.size() * sizeof(long long),
-                         cudaMemcpyHostToDevice));
-    }
+    CKS(ensure_graph_arrays(g));
     CK(g, cudaMemcpyAsync(g->d_bb, hb.data(), hb.size() * sizeof(BlockBatch), cudaMemcpyHostToDevice, st));
     CK(g, cudaMemcpyAsync(g->d_bsrc, hsrc.data(), hsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(g, cudaMemsetAsync(g->d_next, 0, sizeof(unsigned), st));
@@ -1172,6 +1241,70 @@ gbbc_status bc_policy_load(gbbc_graph* g, const float* params, size_t bytes) {
         r = fail(g, GBBC_ERR_CUDA, "policy conversion failed");
     if (r == GBBC_OK && cudaStreamSynchronize(g->last_stream) != cudaSuccess) r = fail(g, GBBC_ERR_CUDA, "sync");
     dfree(g, tmp);
+    return r;
+}
+
+gbbc_status bc_grouping_load(gbbc_graph* g, const float* params, size_t bytes) {
+    if (!g) return GBBC_ERR_INVALID;
+    const int np = (int)bc_mlp_param_count(1);
+    const size_t want = (size_t)np * sizeof(float);
+    if (!params) {
+        if (g->d_grouping) dfree(g, g->d_grouping);
+        g->d_grouping = nullptr;
+        return GBBC_OK;
+    }
+    if (bytes != want) return fail(g, GBBC_ERR_INVALID, "grouping weights: %zu bytes, expected %zu", bytes, want);
+    float* tmp = nullptr;
+    CKS(dalloc(g, (void**)&tmp, want));
+    gbbc_status r = to_device(g, tmp, params, want, g->last_stream);
+    if (r == GBBC_OK && !g->d_grouping) r = dalloc(g, &g->d_grouping, (size_t)np * 2);
+    if (r == GBBC_OK && mlp_to_half(tmp, g->d_grouping, np, g->last_stream) != cudaSuccess)
+        r = fail(g, GBBC_ERR_CUDA, "grouping conversion failed");
+    if (r == GBBC_OK && cudaStreamSynchronize(g->last_stream) != cudaSuccess) r = fail(g, GBBC_ERR_CUDA, "sync");
+    dfree(g, tmp);
+    return r;
+}
+
+namespace {
+gbbc_status grouping_sources(gbbc_graph* g, const int32_t* sources, int64_t k, const void* out,
+                             std::vector<int32_t>& src, std::vector<int32_t>& gid, cudaStream_t st) {
+    if (!g) return GBBC_ERR_INVALID;
+    if (k < 0 || (k > 0 && (!sources || !out))) return fail(g, GBBC_ERR_INVALID, "bad arguments");
+    CKS(to_host(g, src, sources, (size_t)k, st));
+    gid.assign((size_t)k, 0);
+    for (long long i = 0; i < k; ++i) {
+        if (src[i] < 0 || src[i] >= g->n) return fail(g, GBBC_ERR_INVALID, "source %lld outside [0, n)", i);
+        gid[i] = (int32_t)(std::upper_bound(g->goff.begin(), g->goff.end(), (long long)src[i]) - g->goff.begin()) - 1;
+    }
+    return GBBC_OK;
+}
+}  // namespace
+
+gbbc_status bc_grouping_scores(gbbc_graph* g, const int32_t* sources, int64_t k, float* out, void* stream) {
+    if (!g) return GBBC_ERR_INVALID;
+    if (!g->d_grouping) return fail(g, GBBC_ERR_STATE, "no grouping weights loaded");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> src, gid;
+    CKS(grouping_sources(g, sources, k, out, src, gid, st));
+    if (k == 0) return GBBC_OK;
+    std::vector<float> score;
+    CKS(grouping_scores(g, src, gid, score, st));
+    CK(g, cudaMemcpy(out, score.data(), (size_t)k * sizeof(float), cudaMemcpyDefault));
+    return GBBC_OK;
+}
+
+gbbc_status bc_source_features(gbbc_graph* g, const int32_t* sources, int64_t k, float* out, void* stream) {
+    if (!g) return GBBC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> src, gid;
+    CKS(grouping_sources(g, sources, k, out, src, gid, st));
+    if (k == 0) return GBBC_OK;
+    float* d_x = nullptr;
+    CKS(dalloc_t(g, &d_x, (size_t)k * 6));
+    gbbc_status r = source_features(g, src, gid, d_x, st);
+    if (r == GBBC_OK && cudaMemcpy(out, d_x, (size_t)k * 6 * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
+        r = fail(g, GBBC_ERR_CUDA, "copy failed");
+    dfree(g, d_x);
     return r;
 }
 

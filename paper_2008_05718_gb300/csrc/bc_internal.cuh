@@ -171,6 +171,11 @@ cudaError_t launch_block_batches(const Csr& g, const BlockSlots& S, const BlockB
                                  const int32_t* srcs, unsigned* next, u64* bc, int policy, const void* weights_fp16,
                                  const long long* graph_max_deg, unsigned long long* stats, bool start_wide,
                                  cudaStream_t st);
+// Source grouping: features [k][6] and the network's score per source.
+cudaError_t launch_source_features(const Csr& g, const int32_t* src, const int32_t* gid, long long k,
+                                   const long long* goff, const long long* gmaxdeg, float* x, cudaStream_t st);
+cudaError_t launch_group_score(const void* w_half, const float* x, long long k, float* score, cudaStream_t st);
+cudaError_t mlp_to_half(const float* params_dev, void* half_dev, int count, cudaStream_t st);
 // Direction of the step at `level`, whose entries start at q_lo (end: qtail).
 void launch_decide(const Slot& s, long long q_lo, int level, int policy, const void* weights_fp16, long long n_range,
                    long long nnz_range, long long max_deg, cudaStream_t st);

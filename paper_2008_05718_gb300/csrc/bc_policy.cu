@@ -322,6 +322,81 @@ gbbc_status bc_policy_eval(const float* params, const float* x, int64_t n, float
 }  // extern "C"
 
 namespace gbbc {
+
+// ---------------------------------------------------------------------------
+// Source-grouping features (a warp per source): log-scaled degree of s, sum
+// and maximum of its neighbours' degrees, and the size, mean degree and
+// maximum degree of s's graph.
+__global__ void k_source_features(Csr g, const int32_t* src, const int32_t* gid, long long k, const long long* goff,
+                                  const long long* gmaxdeg, float* x) {
+    const int lane = threadIdx.x & 31;
+    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = wid; i < k; i += nw) {
+        int32_t s = src[i];
+        int gi = gid[i];
+        int32_t beg = g.row_ptr[s], end = g.row_ptr[s + 1];
+        unsigned long long sum = 0;
+        int mx = 0;
+        for (int32_t p = beg + lane; p < end; p += 32) {
+            int32_t u = g.col[p];
+            int d = g.row_ptr[u + 1] - g.row_ptr[u];
+            sum += (unsigned long long)d;
+            mx = d > mx ? d : mx;
+        }
+        for (int o = 16; o >= 1; o >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            int om = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = om > mx ? om : mx;
+        }
+        if (lane == 0) {
+            float n = (float)(goff[gi + 1] - goff[gi]);
+            float nnz = (float)(g.row_ptr[goff[gi + 1]] - g.row_ptr[goff[gi]]);
+            float* xi = x + i * kMlpIn;
+            xi[0] = log2p1((float)(end - beg)) / 24.f;
+            xi[1] = log2p1((float)sum) / 32.f;
+            xi[2] = log2p1((float)mx) / 24.f;
+            xi[3] = log2p1(n) / 32.f;
+            xi[4] = log2p1(nnz / (n > 0.f ? n : 1.f)) / 16.f;
+            xi[5] = log2p1((float)gmaxdeg[gi]) / 24.f;
+        }
+    }
+}
+
+// Grouping score (the network's single output) of each feature vector.
+__global__ void k_group_score(const __half* w, const float* x, long long k, float* score) {
+    const int lane = threadIdx.x & 31;
+    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = wid; i < k; i += nw) {
+        float xv[kMlpIn];
+        for (int j = 0; j < kMlpIn; ++j) xv[j] = x[i * kMlpIn + j];
+        float out[1];
+        mlp_warp_eval(w, 1, xv, out);
+        if (lane == 0) score[i] = out[0];
+    }
+}
+
+cudaError_t launch_source_features(const Csr& g, const int32_t* src, const int32_t* gid, long long k,
+                                   const long long* goff, const long long* gmaxdeg, float* x, cudaStream_t st) {
+    if (k <= 0) return cudaSuccess;
+    long long blocks = (k * 32 + 255) / 256;
+    k_source_features<<<(int)(blocks > 4096 ? 4096 : blocks), 256, 0, st>>>(g, src, gid, k, goff, gmaxdeg, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_score(const void* w_half, const float* x, long long k, float* score, cudaStream_t st) {
+    if (k <= 0) return cudaSuccess;
+    long long blocks = (k * 32 + 255) / 256;
+    k_group_score<<<(int)(blocks > 4096 ? 4096 : blocks), 256, 0, st>>>((const __half*)w_half, x, k, score);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_to_half(const float* params_dev, void* half_dev, int count, cudaStream_t st) {
+    k_to_half<<<(count + 255) / 256, 256, 0, st>>>(params_dev, (__half*)half_dev, count);
+    return cudaGetLastError();
+}
+
 // FP16 copy of a direction network for a handle (bc_policy_load).
 cudaError_t policy_to_half(const float* params_dev, void* half_dev, cudaStream_t st) {
     k_to_half<<<(mlp_params(2) + 255) / 256, 256, 0, st>>>(params_dev, (__half*)half_dev, mlp_params(2));

@@ -31,7 +31,8 @@ EXPORTS = ("bc_options_init", "bc_graph_create", "bc_graph_create_multi", "bc_co
            "bc_read", "bc_read_source_state", "bc_reset", "bc_sync", "bc_graph_destroy", "bc_status_string",
            "bc_last_error_detail", "bc_get_stats", "bc_get_trace", "bc_clear_trace", "bc_get_profile",
            "bc_compute_noalloc", "bc_mlp_param_count", "bc_mlp_forward", "bc_mlp_loss_grad", "bc_mlp_adam_step",
-           "bc_mlp_train", "bc_policy_eval", "bc_policy_load", "bc_read_fixed")
+           "bc_mlp_train", "bc_policy_eval", "bc_policy_load", "bc_read_fixed", "bc_source_features",
+           "bc_grouping_load", "bc_grouping_scores")
 NOALLOC_MAX_VERTICES = 16384
 
 
@@ -115,6 +116,9 @@ def load():
             "bc_mlp_train": (ctypes.c_int, [vp, i32, vp, vp, vp, i64, i32, i32, ctypes.c_float, vp, vp]),
             "bc_policy_eval": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
             "bc_policy_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+            "bc_grouping_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+            "bc_source_features": (ctypes.c_int, [vp, vp, i64, vp, vp]),
+            "bc_grouping_scores": (ctypes.c_int, [vp, vp, i64, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -403,6 +407,31 @@ def bc_policy_load(handle, params):
         _check(load().bc_policy_load(handle, a.ctypes.data, a.nbytes), handle)
 
 
+def bc_source_features(handle, sources, stream=None):
+    """Grouping features [k, 6] (float32) of the given sources."""
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    out = np.zeros((len(src), 6), np.float32)
+    _check(load().bc_source_features(handle, src.ctypes.data, len(src), out.ctypes.data, _stream(stream)), handle)
+    return out
+
+
+def bc_grouping_scores(handle, sources, stream=None):
+    """Scores [k] (float32) the loaded grouping network gives the sources."""
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    out = np.zeros(len(src), np.float32)
+    _check(load().bc_grouping_scores(handle, src.ctypes.data, len(src), out.ctypes.data, _stream(stream)), handle)
+    return out
+
+
+def bc_grouping_load(handle, params):
+    """Load FP32 grouping-network parameters (k_out = 1); None unloads."""
+    if params is None:
+        _check(load().bc_grouping_load(handle, None, 0), handle)
+        return
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().bc_grouping_load(handle, a.ctypes.data, a.nbytes), handle)
+
+
 def bc_compute_noalloc(n, nnz, row_ptr, col, sources, bc_out, stream=None):
     """Add the BC dependencies of `sources` (host int32) into bc_out (device
     float64[n]) for the CSR in device memory, without allocating anything
@@ -489,6 +518,16 @@ class BC:
     def load_policy(self, params):
         bc_policy_load(self.h, params)
         return self
+
+    def load_grouping(self, params):
+        bc_grouping_load(self.h, params)
+        return self
+
+    def source_features(self, sources):
+        return bc_source_features(self.h, sources)
+
+    def grouping_scores(self, sources):
+        return bc_grouping_scores(self.h, sources)
 
     def close(self):
         if self.h:

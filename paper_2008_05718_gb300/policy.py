@@ -12,7 +12,8 @@ own CUDA kernels (bc_mlp_train: forward, backward and Adam on the device).
     python -m paper_2008_05718_gb300.policy eval    # learned vs threshold rule
 
 The shipped weights (policy_weights.f32, FP32, bc_mlp_param_count(2) values)
-are what GBBC_POLICY_AUTO and "learned" load by default in the binding.
+are loaded with BC.load_policy (bench.py does so by default); a handle with
+them loaded and GBBC_POLICY_AUTO uses the network, else the threshold rule.
 """
 from __future__ import annotations
 

@@ -17,3 +17,15 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU and libgbbc.so")
     config.addinivalue_line("markers", "slow: CPU test that takes more than a few seconds")
+
+
+@pytest.fixture(scope="session")
+def gb():
+    """The CUDA library's binding, built for this machine (skips without a GPU)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_05718_gb300 import _build, gbbc
+    _build.build()
+    gbbc.load()
+    return gbbc

@@ -16,16 +16,6 @@ pytestmark = pytest.mark.gpu
 REL, ABS = 1e-12, 1e-15
 
 
-@pytest.fixture(scope="module")
-def gb():
-    torch = pytest.importorskip("torch")
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from paper_2008_05718_gb300 import _build, gbbc
-    _build.build()
-    gbbc.load()
-    return gbbc
-
 
 def assert_bc_close(got, want):
     got = np.asarray(got)

@@ -44,16 +44,6 @@ def test_reference_layout_and_adam():
 
 # ---- GPU: training and inference kernels against the reference --------------
 
-@pytest.fixture(scope="module")
-def gb():
-    torch = pytest.importorskip("torch")
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from paper_2008_05718_gb300 import _build, gbbc
-    _build.build()
-    gbbc.load()
-    return gbbc
-
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("k,kind", [(2, 0), (1, 1)])
