@@ -174,9 +174,9 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_from_profiles(kernel_kind, workload):
+def traffic_from_profiles(kernel_kind, workload, grouping):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+    on the current kernel source with the same source grouping (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_kind}_{workload}.txt")
     if not os.path.exists(path):
         return None
@@ -187,7 +187,7 @@ def traffic_from_profiles(kernel_kind, workload):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha256_16") != h:
+    if vals.get("kernel_source_sha256_16") != h or vals.get("source_grouping", "list order") != grouping:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -296,7 +296,7 @@ def run_ours(args):
     p = prof[kind]
     peak, peak_src = measured_peaks()
     achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] > 0 else 0.0
-    tr = traffic_from_profiles(kind, args.workload)
+    tr = traffic_from_profiles(kind, args.workload, "learned" if gweights is not None else "list order")
     total_ms = sum(v["ms"] for v in prof.values())
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": tr, "kernel": kind, "launches_per_step": p["launches"],

@@ -39,7 +39,8 @@ struct gbbc_graph {
     std::vector<long long> goff;     // graph vertex offsets (count + 1)
     u64* d_bc = nullptr;             // [2n] BC in 128-bit fixed point (units 2^-64)
     double* d_bc_out = nullptr;      // [n] staging for bc_read into host memory
-    bool wide_sticky = false;        // batches start in the wide sigma format
+    std::vector<char> wide_graph;    // per graph: its batches start in the wide sigma format
+    int* d_gwide = nullptr;          // per graph: set by the block schedule when a batch went wide
     Slot slot;
     bool slot_ready = false;
     PlainState plain;            // batch width 1
@@ -379,16 +380,16 @@ gbbc_status run_batch_once(gbbc_graph* g, const BatchDesc& b, cudaStream_t st, b
 // wide format (which keeps sigma mod 2^64 as well) and later batches start
 // wide.  The backward only runs once, on the final forward.
 gbbc_status run_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
-    bool wide = g->wide_sticky;
+    bool wide = g->wide_graph[b.gi] != 0;
     if (wide) CKS(alloc_wide(g));
     bool need_wide = false;
     CKS(run_batch_once(g, b, st, wide, &need_wide));
     if (need_wide) {
         CKS(alloc_wide(g));
-        g->wide_sticky = true;
+        g->wide_graph[b.gi] = 1;  // later batches of this graph start wide
         CKS(run_batch_once(g, b, st, true, &need_wide));
     }
-    if (g->wide_sticky) g->stats.wide_batches++;
+    if (g->wide_graph[b.gi]) g->stats.wide_batches++;
     return GBBC_OK;
 }
 
@@ -550,6 +551,7 @@ gbbc_status run_batch_once(gbbc_graph* g, const BatchDesc& b, cudaStream_t st, b
             CKS(resolve(g, pend));
         }
         if (new_n == 0) break;  // no vertex reached at level+1
+        if (s.hctr->carry && !wide) break;  // a lane passed 2^64: stop here, rerun wide
         off.push_back(new_hi);
         nv.push_back(new_n);
         ne.push_back(new_e);
@@ -856,6 +858,8 @@ gbbc_status run_block_mode(gbbc_graph* g, const BatchDesc* bs, int nb, cudaStrea
         hb[i].hi = bs[i].hi;
         hb[i].nsrc = bs[i].nsrc;
         hb[i].src_off = (long long)hsrc.size();
+        hb[i].wide = g->wide_graph[bs[i].gi];
+        hb[i].pad = 0;
         hsrc.insert(hsrc.end(), bs[i].src, bs[i].src + bs[i].nsrc);
     }
     // clusters: few batches get several SMs each (up to 8 CTAs, the portable
@@ -876,19 +880,27 @@ gbbc_status run_block_mode(gbbc_graph* g, const BatchDesc* bs, int nb, cudaStrea
     }
     if (!g->d_next) CKS(dalloc_t(g, &g->d_next, 1));
     if (!g->d_bstats) CKS(dalloc_t(g, &g->d_bstats, 4));
+    const size_t ngraphs = g->wide_graph.size();
+    if (!g->d_gwide) CKS(dalloc_t(g, &g->d_gwide, ngraphs));
     CKS(ensure_graph_arrays(g));
     CK(g, cudaMemcpyAsync(g->d_bb, hb.data(), hb.size() * sizeof(BlockBatch), cudaMemcpyHostToDevice, st));
     CK(g, cudaMemcpyAsync(g->d_bsrc, hsrc.data(), hsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(g, cudaMemsetAsync(g->d_next, 0, sizeof(unsigned), st));
     CK(g, cudaMemsetAsync(g->d_bstats, 0, 4 * sizeof(unsigned long long), st));
+    // batches are taken from a work list, so a slot may get none; its counters
+    // (read below) must then be zero rather than whatever the memory held
+    CK(g, cudaMemsetAsync(g->blk.ctr, 0, (size_t)g->blk.count * sizeof(Counters), st));
+    CK(g, cudaMemsetAsync(g->d_gwide, 0, ngraphs * sizeof(int), st));
     Csr c{g->n, g->nnz, g->d_row_ptr, g->d_col};
     CK(g, launch_block_batches(c, g->blk, g->d_bb, nb, g->d_bsrc, g->d_next, g->d_bc, effective_policy(g),
-                               g->d_policy, g->d_graph_max_deg, g->d_bstats, g->wide_sticky, st));
+                               g->d_policy, g->d_graph_max_deg, g->d_bstats, g->d_gwide, st));
     g->stats.kernel_launches++;
     unsigned long long hst[4];
     CK(g, cudaMemcpyAsync(hst, g->d_bstats, sizeof(hst), cudaMemcpyDeviceToHost, st));
     std::vector<Counters> hc((size_t)g->blk.count);
     CK(g, cudaMemcpyAsync(hc.data(), g->blk.ctr, hc.size() * sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    std::vector<int> gw(ngraphs);
+    CK(g, cudaMemcpyAsync(gw.data(), g->d_gwide, ngraphs * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(g, cudaStreamSynchronize(st));
     for (const Counters& x : hc)
         if (x.err) return fail(g, GBBC_ERR_CAPACITY, "block schedule: queue capacity exceeded (flags %u)", x.err);
@@ -898,8 +910,10 @@ gbbc_status run_block_mode(gbbc_graph* g, const BatchDesc* bs, int nb, cudaStrea
     g->stats.levels_fwd += (long long)hst[1];
     g->stats.levels_pull += (long long)hst[2];
     g->stats.levels_push += (long long)(hst[1] - hst[2]);
-    g->stats.wide_batches += g->wide_sticky ? (long long)nb : (long long)hst[3];
-    if (hst[3] > 0) g->wide_sticky = true;  // later batches start wide
+    for (int i = 0; i < nb; ++i) g->stats.wide_batches += hb[i].wide;
+    g->stats.wide_batches += (long long)hst[3];
+    for (size_t i = 0; i < ngraphs; ++i)
+        if (gw[i]) g->wide_graph[i] = 1;  // later batches of this graph start wide
     g->stats.block_slots = g->blk.count;
     return GBBC_OK;
 }
@@ -926,8 +940,8 @@ bool grid_graph(const gbbc_graph* g, const BatchDesc& b) {
 // Grid or block for each batch: fixed by the options, forced to grid when
 // per-level state is kept or traced.  Under GBBC_SCHEDULE_AUTO, batches of
 // large dense graphs (grid_graph) run grid; the others run block unless a
-// timed trial (the call's first batches, whose results are kept: one in
-// grid, one wave in block) shows grid faster; the choice is kept per handle.
+// timed trial (batches spread over the call's list, whose results are kept)
+// shows grid faster; the choice is kept per handle.
 gbbc_status dispatch(gbbc_graph* g, const std::vector<BatchDesc>& bs, cudaStream_t st) {
     int sched = g->opt.schedule;
     if (g->k_dist || (g->opt.flags & GBBC_TRACE)) sched = GBBC_SCHEDULE_GRID;
@@ -938,31 +952,65 @@ gbbc_status dispatch(gbbc_graph* g, const std::vector<BatchDesc>& bs, cudaStream
         (sched == GBBC_SCHEDULE_BLOCK ? small : large) = bs;
     }
     int small_sched = sched == GBBC_SCHEDULE_AUTO ? g->tuned_schedule : sched;
-    size_t done = 0;
     if (!small.empty() && small_sched == 0) {
         if (small.size() >= 2) {
+            // Timed trial on batches spread evenly over the list (the list may
+            // be sorted by cost, e.g. by the grouping network): one in the grid
+            // schedule (three from 32 batches on), one wave of up to nsm in the
+            // block schedule.
+            // Throughput is compared in source-edge units, since the batches
+            // of a multi-graph handle differ in size.  The trial's results are
+            // kept; the other batches follow in list order.
+            const size_t m = small.size();
+            std::vector<char> used(m, 0);
+            std::vector<BatchDesc> tg, tb, rest;
+            auto work = [&](const BatchDesc& b) {
+                return (double)b.nsrc * (1.0 + (double)(g->h_row_ptr[b.hi] - g->h_row_ptr[b.lo]));
+            };
+            const size_t ngrid = m >= 32 ? 3 : 1;
+            for (size_t j = 0; j < ngrid; ++j) {
+                size_t i = (size_t)(((double)j + 0.5) * (double)m / (double)ngrid);
+                if (i < m && !used[i]) used[i] = 1, tg.push_back(small[i]);
+            }
+            const size_t nblk = std::min<size_t>(m - tg.size(), (size_t)g->nsm);
+            for (size_t j = 0; j < nblk; ++j) {
+                size_t i = (size_t)(((double)j + 0.5) * (double)m / (double)nblk);
+                while (i < m && used[i]) ++i;
+                if (i >= m) {
+                    i = 0;
+                    while (i < m && used[i]) ++i;
+                }
+                if (i < m) used[i] = 1, tb.push_back(small[i]);
+            }
+            for (size_t i = 0; i < m; ++i)
+                if (!used[i]) rest.push_back(small[i]);
             CKS(alloc_slot(g));
             CK(g, cudaStreamSynchronize(st));
+            double w_grid = 0, w_block = 0;
             double t0 = now_s();
-            CKS(run_batch(g, small[0], st));
+            for (const BatchDesc& b : tg) {
+                CKS(run_batch(g, b, st));
+                w_grid += work(b);
+            }
             CK(g, cudaStreamSynchronize(st));
             double t_grid = now_s() - t0;
-            int nblk = (int)std::min<size_t>(small.size() - 1, (size_t)g->nsm);
+            for (const BatchDesc& b : tb) w_block += work(b);
             t0 = now_s();
-            CKS(run_block_mode(g, small.data() + 1, nblk, st));
-            double t_block = (now_s() - t0) / nblk;
-            done = 1 + (size_t)nblk;
-            g->tuned_schedule = t_block < t_grid ? GBBC_SCHEDULE_BLOCK : GBBC_SCHEDULE_GRID;
+            if (!tb.empty()) CKS(run_block_mode(g, tb.data(), (int)tb.size(), st));
+            double t_block = now_s() - t0;
+            g->tuned_schedule = tb.empty() || w_block / t_block > w_grid / t_grid ? GBBC_SCHEDULE_BLOCK
+                                                                                  : GBBC_SCHEDULE_GRID;
             small_sched = g->tuned_schedule;
+            small.swap(rest);
         } else {
             small_sched = GBBC_SCHEDULE_BLOCK;
         }
     }
     if (small_sched == GBBC_SCHEDULE_BLOCK) {
-        CKS(run_block_mode(g, small.data() + done, (int)(small.size() - done), st));
+        if (!small.empty()) CKS(run_block_mode(g, small.data(), (int)small.size(), st));
     } else {
         CKS(alloc_slot(g));
-        for (size_t i = done; i < small.size(); ++i) CKS(run_batch(g, small[i], st));
+        for (const BatchDesc& b : small) CKS(run_batch(g, b, st));
     }
     if (!large.empty()) {
         CKS(alloc_slot(g));
@@ -976,6 +1024,7 @@ gbbc_status finish_create(gbbc_graph* g, cudaStream_t st) {
     bc_clear_trace(g);
     size_t count = g->goff.size() - 1;
     g->graph_max_deg.assign(count, 0);
+    g->wide_graph.assign(count, 0);
     for (size_t i = 0; i < count; ++i)
         for (long long v = g->goff[i]; v < g->goff[i + 1]; ++v)
             g->graph_max_deg[i] = std::max<long long>(g->graph_max_deg[i], g->h_row_ptr[v + 1] - g->h_row_ptr[v]);

@@ -124,6 +124,8 @@ constexpr int kBlockThreads = 512;
 struct BlockBatch {
     int32_t gi, lo, hi, nsrc;
     long long src_off;   // first source of the batch in the source array
+    int32_t wide;        // start in the wide sigma format
+    int32_t pad;
 };
 
 struct BlockSlots {
@@ -166,10 +168,11 @@ void launch_keep_sigma(const Slot& s, int32_t lo, int32_t hi, uint64_t* sigma, u
 void launch_undo(const Slot& s, long long q_lo, long long q_hi, cudaStream_t st);
 // Block-per-batch persistent kernel over `nb` batches; stats[0..3]: batches,
 // forward levels, bottom-up levels, wide reruns (device, accumulated).
-// start_wide runs every batch in the wide sigma format from the start.
+// A batch with .wide set starts in the wide sigma format; one that has to be
+// rerun wide sets gwide[its graph] = 1.
 cudaError_t launch_block_batches(const Csr& g, const BlockSlots& S, const BlockBatch* batches, int nb,
                                  const int32_t* srcs, unsigned* next, u64* bc, int policy, const void* weights_fp16,
-                                 const long long* graph_max_deg, unsigned long long* stats, bool start_wide,
+                                 const long long* graph_max_deg, unsigned long long* stats, int* gwide,
                                  cudaStream_t st);
 // Source grouping: features [k][6] and the network's score per source.
 cudaError_t launch_source_features(const Csr& g, const int32_t* src, const int32_t* gid, long long k,

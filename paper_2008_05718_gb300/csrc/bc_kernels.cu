@@ -1407,6 +1407,10 @@ __device__ bool block_batch(const Csr& g, const Slot& s, long long* lev, unsigne
             if (lane == 0 && lsum) atomicAdd(&s.ctr->lane_sum, lsum);
         }
         csync();
+        // a lane passed 2^64 in this gather: the narrow pass stops here and
+        // the batch is rerun in the wide format (every thread reads the flag
+        // after the same cluster barrier, so all of them leave together)
+        if (!WIDE && ld_cg(&s.ctr->carry)) break;
         if (lead && tid < 32) decide_step(s.ctr, q_hi, level + 1, policy, wts, n_range, nnz_range, max_deg);
         csync();
         ++level;
@@ -1459,7 +1463,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_batches(Csr g, BlockSlo
                                                                  int nb, const int32_t* srcs, unsigned* next,
                                                                  u64* bc, int policy, const __half* wts,
                                                                  const long long* gmaxdeg,
-                                                                 unsigned long long* stats, int start_wide,
+                                                                 unsigned long long* stats, int* gwide,
                                                                  int* slot_batch) {
     extern __shared__ unsigned char dsm[];
     BwdWarpSmem* smem = reinterpret_cast<BwdWarpSmem*>(dsm);
@@ -1479,10 +1483,13 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_batches(Csr g, BlockSlo
         const BlockBatch bb = batches[b];
         const Slot v = slot_view(S, slot, bb.lo);
         const float md = (float)gmaxdeg[bb.gi];
-        if (start_wide || !block_batch<false>(g, v, lev, lsp, bb, srcs + bb.src_off, bc, policy, wts, md, sm, sh,
-                                              stats)) {
+        if (bb.wide || !block_batch<false>(g, v, lev, lsp, bb, srcs + bb.src_off, bc, policy, wts, md, sm, sh,
+                                           stats)) {
             csync();
-            if (rank == 0 && threadIdx.x == 0 && !start_wide) atomicAdd(stats + 3, 1ull);
+            if (rank == 0 && threadIdx.x == 0 && !bb.wide) {
+                atomicAdd(stats + 3, 1ull);
+                gwide[bb.gi] = 1;
+            }
             block_batch<true>(g, v, lev, lsp, bb, srcs + bb.src_off, bc, policy, wts, md, sm, sh, stats);
         }
         if (rank == 0 && threadIdx.x == 0) atomicAdd(stats, 1ull);
@@ -1492,7 +1499,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_batches(Csr g, BlockSlo
 
 cudaError_t launch_block_batches(const Csr& g, const BlockSlots& S, const BlockBatch* batches, int nb,
                                  const int32_t* srcs, unsigned* next, u64* bc, int policy, const void* weights_fp16,
-                                 const long long* graph_max_deg, unsigned long long* stats, bool start_wide,
+                                 const long long* graph_max_deg, unsigned long long* stats, int* gwide,
                                  cudaStream_t st) {
     const size_t smem = (size_t)(kBlockThreads / kWarp) * sizeof(BwdWarpSmem);
     cudaError_t e = cudaFuncSetAttribute(k_block_batches, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1513,9 +1520,8 @@ cudaError_t launch_block_batches(const Csr& g, const BlockSlots& S, const BlockB
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    int start = start_wide ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, k_block_batches, g, S, batches, nb, srcs, next, bc, policy,
-                              (const __half*)weights_fp16, graph_max_deg, stats, start, S.slot_batch);
+                              (const __half*)weights_fp16, graph_max_deg, stats, gwide, S.slot_batch);
 }
 
 // ---------------------------------------------------------------------------

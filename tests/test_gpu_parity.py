@@ -296,6 +296,47 @@ def test_block_schedule_parity_and_identical_bits(gb, make, k, policy):
     assert np.array_equal(blk, grid)
 
 
+def test_block_schedule_with_idle_slots(gb):
+    # one long batch (a path) and many one-level batches (isolated vertices):
+    # clusters that start late find the work list empty and run no batch; their
+    # slots' counters must not be read as errors.  Device memory is dirtied
+    # first by a handle that is then destroyed, so fresh allocations may hold
+    # old bytes.
+    n_path, n_iso = 3000, 64 * 15
+    g = gg.from_edges(n_path + n_iso, [(i, i + 1) for i in range(n_path - 1)])
+    S = np.concatenate([gg.sample_sources(n_path, 64, seed=91), np.arange(n_path, n_path + n_iso)]).astype(np.int32)
+    want, _ = oracle.bc_graph(g, S)
+    for rep in range(3):
+        h = gg.rmat(12, 16, seed=92 + rep)
+        with gb.BC.from_graph(h, schedule="block") as bc:
+            bc.compute(gg.sample_sources(h.n, 512, seed=93))
+            bc.sync()
+        got, _, st = run_gpu(gb, g, S, schedule="block")
+        assert st["schedule"] == 2
+        assert_bc_close(got, want)
+
+
+@pytest.mark.parametrize("schedule", ["block", "grid"])
+def test_wide_format_is_chosen_per_graph(gb, schedule):
+    # the grid's batches pass 2^64 and are rerun wide; the R-MAT graph's are
+    # not, in this call or the next (where the grid's batches start wide)
+    graphs = [gg.rmat(10, 16, seed=95), gg.grid(64, "0.03", seed=96)]
+    per = [gg.sample_sources(g.n, 128, seed=97) for g in graphs]
+    gids = np.repeat(np.arange(2, dtype=np.int32), 128)
+    locs = np.concatenate(per).astype(np.int32)
+    with gb.BC.from_graphs(graphs, schedule=schedule) as bc:
+        bc.compute_multi(gids, locs)
+        assert bc.stats()["wide_batches"] == 2
+        first = [bc.read_fixed(i) for i in range(2)]
+        bc.reset()
+        bc.compute_multi(gids, locs)
+        assert bc.stats()["wide_batches"] == 4
+        assert all(np.array_equal(bc.read_fixed(i), first[i]) for i in range(2))
+        for i, g in enumerate(graphs):
+            want, _ = oracle.bc_graph(g, per[i])
+            assert_bc_close(bc.read(graph_id=i), want)
+
+
 def test_block_schedule_multi_graph_and_width32(gb):
     graphs = [gg.rmat(10, 16, seed=71), gg.grid(40, "0.03", seed=72), gg.path(50), gg.rmat(11, 16, seed=73)]
     gids, locs, per = [], [], []
