@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -40,6 +41,7 @@ struct gbbc_graph {
     u64* d_bc = nullptr;             // [2n] BC in 128-bit fixed point (units 2^-64)
     double* d_bc_out = nullptr;      // [n] staging for bc_read into host memory
     std::vector<char> wide_graph;    // per graph: its batches start in the wide sigma format
+    int max_clusters[4] = {0, 0, 0, 0};  // resident block-schedule clusters of 1, 2, 4, 8 CTAs
     int* d_gwide = nullptr;          // per graph: set by the block schedule when a batch went wide
     Slot slot;
     bool slot_ready = false;
@@ -846,6 +848,21 @@ gbbc_status grouping_scores(gbbc_graph* g, const std::vector<int32_t>& src, cons
     return r;
 }
 
+int ilog2(int x) {
+    int r = 0;
+    while (x > 1) x >>= 1, ++r;
+    return r;
+}
+
+// Cluster size of the block schedule for nb batches (see run_block_mode).
+int block_csize(gbbc_graph* g, int nb) {
+    if (g->max_clusters[0] == 0)
+        for (int i = 0; i < 4; ++i) g->max_clusters[i] = std::max(1, block_max_clusters(1 << i));
+    int csize = 1;
+    while (csize < 8 && (long long)nb * csize * 2 <= g->nsm) csize *= 2;
+    return csize;
+}
+
 gbbc_status run_block_mode(gbbc_graph* g, const BatchDesc* bs, int nb, cudaStream_t st) {
     if (nb <= 0) return GBBC_OK;
     long long nslot = 1;
@@ -862,11 +879,37 @@ gbbc_status run_block_mode(gbbc_graph* g, const BatchDesc* bs, int nb, cudaStrea
         hb[i].pad = 0;
         hsrc.insert(hsrc.end(), bs[i].src, bs[i].src + bs[i].nsrc);
     }
+    // Longest batches first (the work list hands them out in this order), so
+    // that the last batches to start are short ones and no cluster runs alone
+    // at the end.  Estimated cost: edges and vertices of the batch's graph
+    // times a level count (about sqrt(n) on sparse, road-like graphs, log2(n)
+    // otherwise), tripled in the wide sigma format.  BC does not depend on
+    // the order.
+    {
+        std::vector<double> cost((size_t)nb);
+        for (int i = 0; i < nb; ++i) {
+            const double nr = (double)hb[i].hi - hb[i].lo;
+            const double er = (double)(g->h_row_ptr[hb[i].hi] - g->h_row_ptr[hb[i].lo]);
+            const double levels = er <= 6.0 * nr ? std::sqrt(nr) : std::log2(nr + 2.0);
+            cost[i] = (er + nr) * levels * (hb[i].wide ? 3.0 : 1.0) * (double)hb[i].nsrc;
+        }
+        std::vector<int> ord((size_t)nb);
+        for (int i = 0; i < nb; ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        std::vector<BlockBatch> sorted((size_t)nb);
+        for (int i = 0; i < nb; ++i) sorted[i] = hb[ord[i]];
+        hb.swap(sorted);
+    }
     // clusters: few batches get several SMs each (up to 8 CTAs, the portable
-    // cluster size), many batches one SM each
-    int csize = 1;
-    while (csize < 8 && (long long)nb * csize * 2 <= g->nsm) csize *= 2;
-    CKS(alloc_block(g, nslot, std::max(1, std::min(nb, g->nsm / csize))));
+    // cluster size), many batches one SM each.  A batch's time falls about in
+    // proportion to its cluster's CTAs (measured on the 1024^2 grid: 8 CTAs
+    // 1.1 s, 4 CTAs 2.3 s), so the larger cluster wins even when fewer of its
+    // clusters are resident (they are placed within GPCs: 15 of 8 CTAs fit)
+    // and a batch waits for a second round.  Slots beyond the resident
+    // clusters would only hold memory.
+    int csize = block_csize(g, nb);
+    const int resident = g->max_clusters[ilog2(csize)];
+    CKS(alloc_block(g, nslot, std::max(1, std::min(nb, std::min(resident, g->nsm / csize)))));
     g->blk.csize = csize;
     if (g->d_bb_cap < nb) {
         dfree(g, g->d_bb);
@@ -953,7 +996,13 @@ gbbc_status dispatch(gbbc_graph* g, const std::vector<BatchDesc>& bs, cudaStream
     }
     int small_sched = sched == GBBC_SCHEDULE_AUTO ? g->tuned_schedule : sched;
     if (!small.empty() && small_sched == 0) {
-        if (small.size() >= 2) {
+        if (small.size() >= (size_t)std::max(2, g->nsm / 4)) {
+            // enough batches to give every SM a cluster of its own: the grid
+            // schedule, one batch at a time with a read-back per level, cannot
+            // win, and a trial of it on a long batch would cost seconds
+            g->tuned_schedule = GBBC_SCHEDULE_BLOCK;
+            small_sched = GBBC_SCHEDULE_BLOCK;
+        } else if (small.size() >= 2) {
             // Timed trial on batches spread evenly over the list (the list may
             // be sorted by cost, e.g. by the grouping network): one in the grid
             // schedule (three from 32 batches on), one wave of up to nsm in the
@@ -1007,6 +1056,24 @@ gbbc_status dispatch(gbbc_graph* g, const std::vector<BatchDesc>& bs, cudaStream
         }
     }
     if (small_sched == GBBC_SCHEDULE_BLOCK) {
+        // A few batches beyond a whole number of resident-cluster rounds would
+        // each run a last round alone on one cluster.  On large graphs the
+        // grid schedule runs such a batch on the whole GPU in about half that
+        // time (1024^2 grid: 0.37 s against 0.75 s), so they go there.
+        const int nb = (int)small.size();
+        if (nb > 0) {
+            const int csize = block_csize(g, nb);
+            const int R = std::max(1, std::min(g->max_clusters[ilog2(csize)], g->nsm / csize));
+            const int rounds = (nb + R - 1) / R;
+            const int left = nb - (rounds - 1) * R;
+            long long nmin = LLONG_MAX;
+            for (const BatchDesc& b : small) nmin = std::min<long long>(nmin, (long long)b.hi - b.lo);
+            if (rounds >= 2 && left <= R / 4 && nmin > kBlockMaxVertices) {
+                CKS(alloc_slot(g));
+                for (int i = nb - left; i < nb; ++i) CKS(run_batch(g, small[i], st));
+                small.resize((size_t)(nb - left));
+            }
+        }
         if (!small.empty()) CKS(run_block_mode(g, small.data(), (int)small.size(), st));
     } else {
         CKS(alloc_slot(g));

@@ -168,6 +168,9 @@ void launch_keep_sigma(const Slot& s, int32_t lo, int32_t hi, uint64_t* sigma, u
 void launch_undo(const Slot& s, long long q_lo, long long q_hi, cudaStream_t st);
 // Block-per-batch persistent kernel over `nb` batches; stats[0..3]: batches,
 // forward levels, bottom-up levels, wide reruns (device, accumulated).
+// Clusters of csize CTAs of k_block_batches that fit on the device at once
+// (0 if the query fails).
+int block_max_clusters(int csize);
 // A batch with .wide set starts in the wide sigma format; one that has to be
 // rerun wide sets gwide[its graph] = 1.
 cudaError_t launch_block_batches(const Csr& g, const BlockSlots& S, const BlockBatch* batches, int nb,

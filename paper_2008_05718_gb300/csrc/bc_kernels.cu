@@ -1497,6 +1497,31 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_batches(Csr g, BlockSlo
     }
 }
 
+int block_max_clusters(int csize) {
+    const size_t smem = (size_t)(kBlockThreads / kWarp) * sizeof(BwdWarpSmem);
+    if (cudaFuncSetAttribute(k_block_batches, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)csize, 1, 1);
+    cfg.blockDim = dim3(kBlockThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_block_batches, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 cudaError_t launch_block_batches(const Csr& g, const BlockSlots& S, const BlockBatch* batches, int nb,
                                  const int32_t* srcs, unsigned* next, u64* bc, int policy, const void* weights_fp16,
                                  const long long* graph_max_deg, unsigned long long* stats, int* gwide,

@@ -337,6 +337,19 @@ def test_wide_format_is_chosen_per_graph(gb, schedule):
             assert_bc_close(bc.read(graph_id=i), want)
 
 
+def test_block_schedule_large_sparse_graph_with_leftover_batches(gb):
+    # 16 batches of a road-like graph above 65,536 vertices: the batches that
+    # do not fill a round of resident 8-CTA clusters run in the grid schedule
+    g = gg.grid(300, "0.05", seed=98)
+    S = gg.sample_sources(g.n, 1024, seed=99)
+    blk, _, st = run_gpu(gb, g, S, schedule="block")
+    assert st["batches"] == 16 and st["wide_batches"] == 16
+    grid, _, _ = run_gpu(gb, g, S, schedule="grid")
+    assert np.array_equal(blk, grid)
+    want, _ = oracle.bc_graph(g, S)
+    assert_bc_close(blk, want)
+
+
 def test_block_schedule_multi_graph_and_width32(gb):
     graphs = [gg.rmat(10, 16, seed=71), gg.grid(40, "0.03", seed=72), gg.path(50), gg.rmat(11, 16, seed=73)]
     gids, locs, per = [], [], []
@@ -360,6 +373,20 @@ def test_autotuned_schedule_gives_identical_bits(gb):
     assert st["schedule"] in (1, 2)
     grid, _, _ = run_gpu(gb, g, S, schedule="grid")
     assert np.array_equal(auto, grid)
+
+
+def test_autotuner_takes_block_schedule_when_batches_fill_the_gpu(gb):
+    # 38 batches of a small graph (each source three times): block schedule
+    # without a timed trial
+    g = gg.rmat(12, 16, seed=82)
+    S1 = gg.sample_sources(g.n, 810, seed=82)
+    S = np.tile(S1, 3)
+    auto, _, st = run_gpu(gb, g, S, schedule="auto")
+    assert st["schedule"] == 2 and st["batches"] == 38
+    grid, _, _ = run_gpu(gb, g, S, schedule="grid")
+    assert np.array_equal(auto, grid)
+    want, _ = oracle.bc_graph(g, S1)
+    assert_bc_close(auto, 3.0 * want)
 
 
 def test_fixed_point_partials_add_to_identical_bits(gb):
