@@ -42,6 +42,11 @@ WORKLOADS = {
     "er4096": "Erdos-Renyi n=4096, p=8/4095, seed 1, all 4096 vertices as sources",
     "grid1024": "1024x1024 4-neighbour grid, 5% edges removed, LCC, seed 3, 1024 uniform sources",
     "rmat22": "R-MAT scale 22, edge factor 16, seed 5, 16,384 uniform sources",
+    "tri1024": "planar triangulation of a 1024x1024 lattice (grid edges plus one random diagonal per cell, "
+               "Delaunay-like, average degree 6), seed 6, 1024 uniform sources",
+    "rgg20": "random geometric graph, 2^20 uniform points, expected degree 10, LCC, seed 7, 1024 uniform sources",
+    "mesh100": "100x100x100 mesh, 27-point stencil (KKT-like banded pattern, average degree 25.5), "
+               "4096 uniform sources (seed 8)",
 }
 
 

@@ -57,6 +57,9 @@ def _load():
                                     ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, P(_CSR)]
             lib.gg_grid.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, P(_CSR)]
             lib.gg_lcc.argtypes = [P(_CSR), P(_CSR), i32p]
+            lib.gg_tri.argtypes = [ctypes.c_int32, ctypes.c_uint64, P(_CSR)]
+            lib.gg_rgg.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P(_CSR)]
+            lib.gg_mesh27.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P(_CSR)]
             lib.gg_sample_sources.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, i32p]
             lib.gg_permutation.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, i32p]
             lib.gg_rng.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
@@ -158,6 +161,46 @@ def grid(side: int, remove_frac="0", seed: int = 0, lcc: bool = True) -> Graph:
     if _load().gg_grid(int(side), int(rm), int(seed), int(bool(lcc)), ctypes.byref(c)) != 0:
         raise MemoryError("gg_grid failed")
     return _take(c, f"grid_{side}", {"removed": rm, "seed": seed})
+
+
+def tri(side: int, seed: int = 0) -> Graph:
+    """Planar triangulation of a side x side lattice (grid edges plus one
+    random diagonal per cell): a Delaunay-like planar graph, average degree
+    about 6, diameter about 2 * side."""
+    c = _CSR()
+    if _load().gg_tri(int(side), int(seed), ctypes.byref(c)) != 0:
+        raise ValueError("gg_tri failed")
+    return _take(c, f"tri{side}", {"side": side, "seed": seed})
+
+
+def rgg_threshold(n: int, avg_deg: float) -> int:
+    """Squared radius, in units of the 2^32-sided square, that gives expected
+    degree avg_deg (boundary effects aside): r^2 = avg_deg / (pi * n)."""
+    import math
+    r2 = int(avg_deg / (math.pi * n) * float(1 << 64))
+    return max(1, min(r2, (1 << 64) - 1))
+
+
+def rgg(n: int, avg_deg: float = 10.0, seed: int = 0, lcc: bool = True) -> Graph:
+    """Random geometric graph on n uniform points of the unit square, an edge
+    where the distance is below r with pi r^2 n = avg_deg; vertices numbered in
+    spatial cell order; the largest component kept by default."""
+    c = _CSR()
+    r2 = rgg_threshold(n, avg_deg)
+    if _load().gg_rgg(int(n), r2, int(seed), 1 if lcc else 0, ctypes.byref(c)) != 0:
+        raise ValueError("gg_rgg failed")
+    return _take(c, f"rgg_n{n}", {"n": n, "avg_deg": avg_deg, "seed": seed, "r2": r2})
+
+
+def mesh27(nx: int, ny: int = None, nz: int = None) -> Graph:
+    """3-D mesh with the 27-point stencil (26 neighbours inside): the banded
+    sparsity of the KKT matrices of 3-D PDE-constrained optimisation."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    c = _CSR()
+    if _load().gg_mesh27(int(nx), int(ny), int(nz), ctypes.byref(c)) != 0:
+        raise ValueError("gg_mesh27 failed")
+    return _take(c, f"mesh27_{nx}x{ny}x{nz}", {"dims": (nx, ny, nz)})
 
 
 def largest_cc(g: Graph) -> tuple[Graph, np.ndarray]:
@@ -265,7 +308,14 @@ def workload(name: str):
     rmat18   : R-MAT scale 18, ef 16, seed 2, 4096 uniform sources.
     grid1024 : 1024^2 grid, 5% edges removed, LCC, seed 3, 1024 uniform sources.
     rmat22   : R-MAT scale 22, ef 16, seed 5, 16384 uniform sources.
-    Small variants for tests: rmat<s> (any scale), grid<side>.
+    tri1024  : planar triangulation of a 1024^2 lattice (Delaunay-like), seed 6,
+               1024 uniform sources.
+    rgg20    : random geometric graph, 2^20 points, expected degree 10, LCC,
+               seed 7, 1024 uniform sources.
+    mesh100  : 100^3 mesh, 27-point stencil (KKT-like), 4096 uniform sources
+               (seed 8).
+    Small variants for tests: rmat<s> (any scale), grid<side>, tri<side>,
+    rgg<log2 n>, mesh<side>.
     """
     if name == "er4096":
         g = er(4096, Fraction(8, 4095), seed=1)
@@ -283,6 +333,21 @@ def workload(name: str):
         side = int(name[4:])
         g = grid(side, Fraction(5, 100), seed=3000 + side)
         return g, sample_sources(g.n, min(256, g.n), seed=3000 + side)
+    if name.startswith("tri"):
+        side = int(name[3:])
+        seed = 6 if side == 1024 else 6000 + side
+        g = tri(side, seed=seed)
+        return g, sample_sources(g.n, min(1024 if side == 1024 else 256, g.n), seed=seed)
+    if name.startswith("rgg"):
+        s = int(name[3:])
+        seed = 7 if s == 20 else 7000 + s
+        g = rgg(1 << s, 10.0, seed=seed)
+        return g, sample_sources(g.n, min(1024 if s == 20 else 256, g.n), seed=seed)
+    if name.startswith("mesh"):
+        side = int(name[4:])
+        g = mesh27(side)
+        seed = 8 if side == 100 else 8000 + side
+        return g, sample_sources(g.n, min(4096 if side == 100 else 256, g.n), seed=seed)
     raise KeyError(name)
 
 

@@ -46,7 +46,7 @@ static inline uint64_t gg_bounded(uint64_t r, uint64_t range) {
     return (uint64_t)(((__uint128_t)r * (__uint128_t)range) >> 64);
 }
 
-enum { ST_ER = 1, ST_RMAT = 2, ST_PERM = 3, ST_GRID = 4, ST_SRC = 5 };
+enum { ST_ER = 1, ST_RMAT = 2, ST_PERM = 3, ST_GRID = 4, ST_SRC = 5, ST_TRI = 6, ST_RGG = 7 };
 
 typedef struct {
     int32_t n;
@@ -350,6 +350,170 @@ int gg_grid(int32_t side, int64_t remove_count, uint64_t seed, int32_t keep_lcc,
     if (!keep_lcc) { *out = full; return 0; }
     rc = gg_lcc(&full, out, NULL);
     gg_free_csr(&full);
+    return rc;
+}
+
+/* Planar triangulation of a side x side point lattice (a Delaunay-like
+ * planar graph): the 4-neighbour grid edges plus one diagonal per unit cell,
+ * (i,j)-(i+1,j+1) or (i,j+1)-(i+1,j) by one random bit per cell.  Interior
+ * vertices have degree 4 + (diagonals at their 4 cells), 6 on average; the
+ * graph is connected.  Vertex (i, j) = i*side + j. */
+int gg_tri(int32_t side, uint64_t seed, gg_csr *out) {
+    memset(out, 0, sizeof(*out));
+    if (side < 1 || (int64_t)side * side >= ((int64_t)1 << 31)) return -1;
+    int64_t cells = (int64_t)(side - 1) * (side - 1);
+    int64_t m = 2 * (int64_t)side * (side - 1) + cells;
+    int32_t *eu = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    int32_t *ev = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    if (!eu || !ev) { free(eu); free(ev); return -1; }
+    uint64_t key = gg_key(seed, ST_TRI);
+    int64_t q = 0;
+    for (int32_t i = 0; i < side; ++i)
+        for (int32_t j = 0; j < side; ++j) {
+            int32_t a = i * side + j;
+            if (j + 1 < side) { eu[q] = a; ev[q] = a + 1; ++q; }
+            if (i + 1 < side) { eu[q] = a; ev[q] = a + side; ++q; }
+            if (i + 1 < side && j + 1 < side) {
+                uint64_t bit = gg_at(key, (uint64_t)i * (uint64_t)(side - 1) + (uint64_t)j) >> 63;
+                if (bit) { eu[q] = a + 1; ev[q] = a + side; }
+                else { eu[q] = a; ev[q] = a + side + 1; }
+                ++q;
+            }
+        }
+    int rc = gg_from_edges(side * side, q, eu, ev, out);
+    free(eu);
+    free(ev);
+    return rc;
+}
+
+static uint64_t isqrt64(uint64_t x) {
+    uint64_t r = 0;
+    for (int b = 31; b >= 0; --b) {
+        uint64_t t = r | (1ULL << b);
+        if ((__uint128_t)t * t <= x) r = t;
+    }
+    return r;
+}
+
+/* Random geometric graph: n points with independent uniform 32-bit integer
+ * coordinates (x, y) in [0, 2^32)^2, an edge between two points whose squared
+ * Euclidean distance is below r2 (exact integer arithmetic).  Points are
+ * binned into square cells of side >= sqrt(r2) and numbered in cell order
+ * (row-major over cells, generation order within a cell), so that vertex ids
+ * follow space; keep_lcc keeps the largest component, renumbered in order. */
+int gg_rgg(int32_t n, uint64_t r2, uint64_t seed, int32_t keep_lcc, gg_csr *out) {
+    memset(out, 0, sizeof(*out));
+    if (n < 1 || r2 == 0) return -1;
+    uint64_t r = isqrt64(r2);
+    if ((__uint128_t)r * r < r2) ++r; /* ceil(sqrt(r2)) */
+    uint64_t cs = r > 0 ? r : 1;     /* cell side */
+    uint64_t C = ((1ULL << 32) + cs - 1) / cs;
+    uint64_t cmax = isqrt64((uint64_t)n);  /* at most about n cells */
+    if (cmax < 1) cmax = 1;
+    if (C > cmax) C = cmax, cs = ((1ULL << 32) + C - 1) / C;
+    uint32_t *px = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    uint32_t *py = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    int64_t *cstart = (int64_t *)calloc((size_t)(C * C + 1), sizeof(int64_t));
+    int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!px || !py || !cstart || !order) {
+        free(px); free(py); free(cstart); free(order);
+        return -1;
+    }
+    uint64_t key = gg_key(seed, ST_RGG);
+    for (int32_t i = 0; i < n; ++i) {
+        px[i] = (uint32_t)(gg_at(key, 2 * (uint64_t)i) >> 32);
+        py[i] = (uint32_t)(gg_at(key, 2 * (uint64_t)i + 1) >> 32);
+        cstart[(py[i] / cs) * C + px[i] / cs + 1]++;
+    }
+    for (uint64_t c = 0; c < C * C; ++c) cstart[c + 1] += cstart[c];
+    {
+        int64_t *fill = (int64_t *)malloc((size_t)(C * C) * sizeof(int64_t));
+        if (!fill) { free(px); free(py); free(cstart); free(order); return -1; }
+        memcpy(fill, cstart, (size_t)(C * C) * sizeof(int64_t));
+        for (int32_t i = 0; i < n; ++i) {
+            int64_t p = fill[(py[i] / cs) * C + px[i] / cs]++;
+            order[p] = i;
+        }
+        free(fill);
+    }
+    /* edges between points of neighbouring cells, each pair once (a < b) */
+    int64_t cap = 1024, m = 0;
+    int32_t *eu = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    int32_t *ev = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    int rc = (eu && ev) ? 0 : -1;
+    for (int64_t p = 0; p < n && rc == 0; ++p) {
+        int32_t i = order[p];
+        int64_t cx = px[i] / cs, cy = py[i] / cs;
+        for (int64_t dy = -1; dy <= 1 && rc == 0; ++dy)
+            for (int64_t dx = -1; dx <= 1; ++dx) {
+                int64_t ux = cx + dx, uy = cy + dy;
+                if (ux < 0 || uy < 0 || ux >= (int64_t)C || uy >= (int64_t)C) continue;
+                int64_t c = uy * (int64_t)C + ux;
+                for (int64_t q = cstart[c]; q < cstart[c + 1]; ++q) {
+                    if (q <= p) continue;
+                    int32_t j = order[q];
+                    int64_t ddx = (int64_t)px[i] - (int64_t)px[j], ddy = (int64_t)py[i] - (int64_t)py[j];
+                    uint64_t adx = (uint64_t)(ddx < 0 ? -ddx : ddx), ady = (uint64_t)(ddy < 0 ? -ddy : ddy);
+                    __uint128_t d2 = (__uint128_t)adx * adx + (__uint128_t)ady * ady;
+                    if (d2 >= (__uint128_t)r2) continue;
+                    if (m == cap) {
+                        cap *= 2;
+                        int32_t *nu = (int32_t *)realloc(eu, (size_t)cap * sizeof(int32_t));
+                        int32_t *nv = nu ? (int32_t *)realloc(ev, (size_t)cap * sizeof(int32_t)) : NULL;
+                        if (nu) eu = nu;
+                        if (nv) ev = nv;
+                        if (!nu || !nv) { rc = -1; break; }
+                    }
+                    eu[m] = (int32_t)p;
+                    ev[m] = (int32_t)q;
+                    ++m;
+                }
+            }
+    }
+    free(px); free(py); free(cstart); free(order);
+    gg_csr full;
+    if (rc == 0) rc = gg_from_edges(n, m, eu, ev, &full);
+    free(eu);
+    free(ev);
+    if (rc) return rc;
+    if (!keep_lcc) { *out = full; return 0; }
+    rc = gg_lcc(&full, out, NULL);
+    gg_free_csr(&full);
+    return rc;
+}
+
+/* 3-D mesh with the 27-point stencil (a banded, KKT-like sparsity pattern):
+ * nx x ny x nz points, each joined to every other point whose coordinates
+ * differ by at most 1 in each dimension (26 neighbours inside).  Vertex
+ * (x, y, z) = (x*ny + y)*nz + z. */
+int gg_mesh27(int32_t nx, int32_t ny, int32_t nz, gg_csr *out) {
+    memset(out, 0, sizeof(*out));
+    if (nx < 1 || ny < 1 || nz < 1) return -1;
+    int64_t n = (int64_t)nx * ny * nz;
+    if (n >= ((int64_t)1 << 31) || 13 * n >= ((int64_t)1 << 31)) return -1;
+    int64_t cap = 13 * n + 1, m = 0;
+    int32_t *eu = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    int32_t *ev = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    if (!eu || !ev) { free(eu); free(ev); return -1; }
+    for (int32_t x = 0; x < nx; ++x)
+        for (int32_t y = 0; y < ny; ++y)
+            for (int32_t z = 0; z < nz; ++z) {
+                int32_t a = (x * ny + y) * nz + z;
+                for (int dx = -1; dx <= 1; ++dx)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dz = -1; dz <= 1; ++dz) {
+                            int32_t X = x + dx, Y = y + dy, Z = z + dz;
+                            if (X < 0 || Y < 0 || Z < 0 || X >= nx || Y >= ny || Z >= nz) continue;
+                            int32_t b = (X * ny + Y) * nz + Z;
+                            if (b <= a) continue;
+                            eu[m] = a;
+                            ev[m] = b;
+                            ++m;
+                        }
+            }
+    int rc = gg_from_edges((int32_t)n, m, eu, ev, out);
+    free(eu);
+    free(ev);
     return rc;
 }
 

@@ -15,6 +15,9 @@ CASES = {
     "rmat14_nopermute": lambda: gg.rmat(14, 16, seed=7, permute=False),
     "grid64": lambda: gg.grid(64, "0.03", seed=64),
     "grid200": lambda: gg.grid(200, "0.05", seed=3),
+    "tri64": lambda: gg.tri(64, seed=6064),
+    "rgg12": lambda: gg.rgg(1 << 12, 10.0, seed=7012),
+    "mesh12": lambda: gg.mesh27(12),
 }
 
 

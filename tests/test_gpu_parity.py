@@ -350,6 +350,25 @@ def test_block_schedule_large_sparse_graph_with_leftover_batches(gb):
     assert_bc_close(blk, want)
 
 
+@pytest.mark.parametrize("make,k", [(lambda: gg.tri(48, seed=101), 200), (lambda: gg.rgg(3000, 10.0, seed=102), 200),
+                                    (lambda: gg.mesh27(12), 200)])
+@pytest.mark.parametrize("schedule", ["grid", "block"])
+def test_planar_geometric_and_mesh_classes(gb, make, k, schedule):
+    # the Delaunay-like, random geometric and KKT-like mesh classes: dist and
+    # sigma bit-exact, BC within tolerance, the same bits in both schedules
+    g = make()
+    S = gg.sample_sources(g.n, k, seed=103)
+    got, _ = check(gb, g, S, keep=(0, k - 1), schedule=schedule)
+    other, _, _ = run_gpu(gb, g, S, schedule="block" if schedule == "grid" else "grid")
+    assert np.array_equal(got, other)
+
+
+@pytest.mark.parametrize("name,nsrc", [("tri1024", 16), ("rgg20", 16), ("mesh100", 8)])
+def test_planar_geometric_and_mesh_full_size_sampled(gb, name, nsrc):
+    g, S = gg.workload(name)
+    check(gb, g, S[:nsrc], keep=(0, nsrc - 1))
+
+
 def test_block_schedule_multi_graph_and_width32(gb):
     graphs = [gg.rmat(10, 16, seed=71), gg.grid(40, "0.03", seed=72), gg.path(50), gg.rmat(11, 16, seed=73)]
     gids, locs, per = [], [], []

@@ -36,9 +36,78 @@ def assert_valid_csr(g):
     lambda: gg.diamond_chain(5),
     lambda: gg.full_grid(7, 9),
     lambda: gg.from_edges(6, [(0, 0), (1, 2), (2, 1), (1, 2), (5, 3)]),
+    lambda: gg.tri(40, seed=6),
+    lambda: gg.rgg(3000, 10.0, seed=7),
+    lambda: gg.rgg(3000, 3.0, seed=7, lcc=False),
+    lambda: gg.mesh27(7, 5, 4),
 ])
 def test_csr_valid(make):
     assert_valid_csr(make())
+
+
+def test_tri_is_a_lattice_triangulation():
+    side = 37
+    g = gg.tri(side, seed=11)
+    assert g.n == side * side
+    cells = (side - 1) ** 2
+    assert g.nnz == 2 * (2 * side * (side - 1) + cells)  # grid edges + one diagonal per cell
+    assert g.nnz // 2 <= 3 * g.n - 6  # planar (Euler)
+    E = {(int(a), int(b)) for a, b in g.edges()}
+    for i in range(side - 1):
+        for j in range(side - 1):
+            a = i * side + j
+            d1 = (a, a + side + 1) in E
+            d2 = (a + 1, a + side) in E
+            assert d1 != d2  # exactly one diagonal per cell
+    deg = g.degrees()
+    assert deg.min() >= 2 and deg.max() <= 8
+    assert 5.7 < deg.mean() < 6.0  # 6 inside, less on the boundary
+
+
+def test_rgg_edges_are_exactly_the_close_pairs():
+    # brute force over all pairs with the generator's own coordinates (the
+    # SplitMix64 stream of the seed), mapped through the spatial numbering
+    import math
+    n, seed = 700, 21
+    g = gg.rgg(n, 10.0, seed=seed, lcc=False)
+    r2 = gg.rgg_threshold(n, 10.0)
+    xs = np.array([gg.rng(seed, 7, 2 * i) >> 32 for i in range(n)], dtype=np.int64)
+    ys = np.array([gg.rng(seed, 7, 2 * i + 1) >> 32 for i in range(n)], dtype=np.int64)
+    cs = math.isqrt(r2)
+    cs += cs * cs < r2
+    C = -(-(1 << 32) // cs)
+    cmax = max(1, math.isqrt(n))
+    if C > cmax:
+        C = cmax
+        cs = -(-(1 << 32) // C)
+    cell = (ys // cs) * C + xs // cs
+    order = np.lexsort((np.arange(n), cell))  # cell order, generation order within a cell
+    new_id = np.empty(n, np.int64)
+    new_id[order] = np.arange(n)
+    want = set()
+    for i in range(n):
+        for j in range(i + 1, n):
+            dx, dy = int(xs[i] - xs[j]), int(ys[i] - ys[j])
+            if dx * dx + dy * dy < r2:
+                a, b = sorted((int(new_id[i]), int(new_id[j])))
+                want.add((a, b))
+    got = {(int(a), int(b)) for a, b in g.edges()}
+    assert got == want
+    assert 7.0 < 2 * len(want) / n < 11.0  # expected degree 10 less the boundary loss
+
+
+def test_mesh27_degrees_closed_form():
+    nx, ny, nz = 6, 5, 4
+    g = gg.mesh27(nx, ny, nz)
+    deg = g.degrees()
+    for x in range(nx):
+        for y in range(ny):
+            for z in range(nz):
+                per = [1 + (c > 0) + (c < m - 1) for c, m in ((x, nx), (y, ny), (z, nz))]
+                assert deg[(x * ny + y) * nz + z] == per[0] * per[1] * per[2] - 1
+    assert g.nnz == deg.sum()
+    # the chebyshev distance is the BFS distance: diameter = max side - 1
+    assert gg.mesh27(9, 3, 2).n == 54
 
 
 def test_goldens_match():
