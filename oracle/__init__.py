@@ -9,8 +9,10 @@ except, in tests, through the separate input generators.
 
   brandes.c  single-threaded Brandes per Algorithm 1, exact (multi-limb)
              sigma, FP64 delta and BC                              -> bc()
+             and its weighted (Dijkstra) form                      -> bc_weighted()
   brute.py   Eq. 1 evaluated by enumerating every shortest path, exact
-             rationals, for graphs with n <= 10                    -> brute
+             rationals, for graphs with n <= 10 (edge counts or
+             weights as path lengths)                              -> brute
   mlp.py     FP64 numpy reference of the policy network (forward, analytic
              gradients, Adam step)                                 -> mlp
 """
@@ -51,6 +53,12 @@ def _load():
                                       P(ctypes.c_int32), P(ctypes.c_uint64), P(ctypes.c_uint8),
                                       P(ctypes.c_double)]
             lib.oracle_bc.restype = ctypes.c_int
+            lib.oracle_bc_weighted.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32),
+                                               P(ctypes.c_int32), ctypes.c_int64, P(ctypes.c_int32),
+                                               P(ctypes.c_double), ctypes.c_int64, P(ctypes.c_int64),
+                                               P(ctypes.c_int32), P(ctypes.c_uint64), P(ctypes.c_uint8),
+                                               P(ctypes.c_double)]
+            lib.oracle_bc_weighted.restype = ctypes.c_int
             lib.oracle_big_to_scaled.argtypes = [P(ctypes.c_uint64), ctypes.c_int32, P(ctypes.c_double),
                                                  P(ctypes.c_int64)]
             lib.oracle_big_to_scaled.restype = None
@@ -97,6 +105,45 @@ def bc(n: int, row_ptr, col, sources, dump=(), bc_init=None):
         raise MemoryError("oracle_bc: allocation failed")
     states = {int(d): SourceState(dist[i], sig[i], ovf[i], dlt[i]) for i, d in enumerate(di)}
     return out, states
+
+
+def bc_weighted(n: int, row_ptr, col, weight, sources, dump=(), bc_init=None):
+    """Weighted Brandes BC (Dijkstra distances, positive integer weights
+    aligned with col) summed over `sources`; returns like bc()."""
+    lib = _load()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    wt = np.ascontiguousarray(weight, dtype=np.int32)
+    if len(wt) != len(cl):
+        raise ValueError("weight must align with col")
+    src = np.ascontiguousarray(sources, dtype=np.int32).reshape(-1)
+    out = np.zeros(n, np.float64) if bc_init is None else np.array(bc_init, np.float64, copy=True)
+    di = np.ascontiguousarray(sorted(set(int(x) for x in dump)), dtype=np.int64)
+    nd = len(di)
+    dist = np.zeros((nd, n), np.int32)
+    sig = np.zeros((nd, n), np.uint64)
+    ovf = np.zeros((nd, n), np.uint8)
+    dlt = np.zeros((nd, n), np.float64)
+    if len(cl) == 0:
+        cl = np.zeros(1, np.int32)
+        wt = np.ones(1, np.int32)
+    rc = lib.oracle_bc_weighted(int(n), _p(rp, ctypes.c_int32), _p(cl, ctypes.c_int32), _p(wt, ctypes.c_int32),
+                                len(src), _p(src, ctypes.c_int32), _p(out, ctypes.c_double), nd,
+                                _p(di, ctypes.c_int64), _p(dist, ctypes.c_int32), _p(sig, ctypes.c_uint64),
+                                _p(ovf, ctypes.c_uint8), _p(dlt, ctypes.c_double))
+    if rc == -1:
+        raise ValueError("oracle_bc_weighted: invalid input (source out of range or weight < 1)")
+    if rc == -3:
+        raise ValueError("oracle_bc_weighted: a distance exceeds 2^31 - 1")
+    if rc != 0:
+        raise MemoryError("oracle_bc_weighted: allocation failed")
+    states = {int(d): SourceState(dist[i], sig[i], ovf[i], dlt[i]) for i, d in enumerate(di)}
+    return out, states
+
+
+def bc_graph_weighted(g, weight, sources, dump=()):
+    """bc_weighted() for a graph object and its weight array."""
+    return bc_weighted(g.n, g.row_ptr, g.col, weight, sources, dump)
 
 
 def bc_graph(g, sources, dump=()):

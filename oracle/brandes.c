@@ -238,3 +238,158 @@ done:
     free(ar.limb);
     return rc;
 }
+
+/*
+ * Weighted form (the SSSP case the paper's forward phase names beside BFS,
+ * Sec. IV-C: "BFS/SSSP"): undirected edges with positive integer weights,
+ * weight[p] belonging to the CSR entry col[p] (symmetric: the two entries of
+ * an edge carry the same weight).  Per source s:
+ *   distances   - Dijkstra from s (binary heap, lazy deletion); the settle
+ *                 order lists the reached vertices by nondecreasing distance.
+ *   sigma       - in settle order, for w != s: sigma[w] = sum of sigma[v]
+ *                 over the neighbours v with dist[v] + weight(v, w) ==
+ *                 dist[w] (its shortest-path predecessors, all settled
+ *                 before w since weights are >= 1); sigma[s] = 1; exact.
+ *   backward    - in reverse settle order, for each such predecessor v of w:
+ *                 delta[v] += sigma[v]/sigma[w] * (1 + delta[w])  (Eq. 2).
+ *   accumulation, dumps, ratio rounding: as in oracle_bc.
+ * Distances are int64 here; the dumps hold them as int32 (-1 unreachable),
+ * and a distance above 2^31 - 1 is an error (-3).
+ */
+typedef struct {
+    int64_t d;
+    int32_t v;
+} heap_item;
+
+static void heap_push(heap_item *h, int64_t *len, int64_t d, int32_t v) {
+    int64_t i = (*len)++;
+    h[i].d = d;
+    h[i].v = v;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (h[p].d <= h[i].d) break;
+        heap_item t = h[p]; h[p] = h[i]; h[i] = t;
+        i = p;
+    }
+}
+
+static heap_item heap_pop(heap_item *h, int64_t *len) {
+    heap_item top = h[0];
+    h[0] = h[--(*len)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < *len && h[l].d < h[m].d) m = l;
+        if (r < *len && h[r].d < h[m].d) m = r;
+        if (m == i) break;
+        heap_item t = h[m]; h[m] = h[i]; h[i] = t;
+        i = m;
+    }
+    return top;
+}
+
+int oracle_bc_weighted(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *weight, int64_t k,
+                       const int32_t *sources, double *bc, int64_t n_dump, const int64_t *dump_idx,
+                       int32_t *dump_dist, uint64_t *dump_sigma, uint8_t *dump_ovf, double *dump_delta) {
+    if (n < 0 || k < 0) return -1;
+    for (int64_t i = 0; i < k; ++i)
+        if (sources[i] < 0 || sources[i] >= n) return -1;
+    if (n == 0) return 0;
+    int64_t nnz = row_ptr[n];
+    for (int64_t p = 0; p < nnz; ++p)
+        if (weight[p] < 1) return -1;
+    int64_t *dist = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    uint8_t *done_v = (uint8_t *)malloc((size_t)n);
+    int64_t *soff = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int32_t *scap = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    double *delta = (double *)malloc((size_t)n * sizeof(double));
+    heap_item *heap = (heap_item *)malloc((size_t)(nnz + 2) * sizeof(heap_item));
+    arena_t ar = {0, 0, 0};
+    int rc = 0;
+    if (!dist || !done_v || !soff || !scap || !order || !delta || !heap) { rc = -2; goto done; }
+
+    for (int64_t si = 0; si < k; ++si) {
+        int32_t s = sources[si];
+        for (int32_t v = 0; v < n; ++v) { dist[v] = -1; done_v[v] = 0; soff[v] = -1; scap[v] = 0; }
+        ar.used = 0;
+        /* ---- distances: Dijkstra ---- */
+        int64_t hl = 0, nset = 0;
+        dist[s] = 0;
+        heap_push(heap, &hl, 0, s);
+        while (hl > 0) {
+            heap_item it = heap_pop(heap, &hl);
+            int32_t u = it.v;
+            if (done_v[u] || it.d != dist[u]) continue; /* stale entry */
+            done_v[u] = 1;
+            order[nset++] = u;
+            for (int32_t p = row_ptr[u]; p < row_ptr[u + 1]; ++p) {
+                int32_t w = col[p];
+                int64_t nd = dist[u] + (int64_t)weight[p];
+                if (!done_v[w] && (dist[w] < 0 || nd < dist[w])) {
+                    dist[w] = nd;
+                    heap_push(heap, &hl, nd, w);
+                }
+            }
+        }
+        for (int64_t q = 0; q < nset; ++q)
+            if (dist[order[q]] > 2147483647LL) { rc = -3; goto done; }
+        /* ---- sigma in settle order, from the predecessors ---- */
+        soff[s] = arena_alloc(&ar, 1);
+        if (soff[s] < 0) { rc = -2; goto done; }
+        ar.limb[soff[s]] = 1;
+        scap[s] = 1;
+        for (int64_t q = 1; q < nset; ++q) {
+            int32_t w = order[q];
+            int32_t maxlen = 1;
+            for (int32_t p = row_ptr[w]; p < row_ptr[w + 1]; ++p) {
+                int32_t v = col[p];
+                if (dist[v] >= 0 && dist[v] + (int64_t)weight[p] == dist[w]) {
+                    int32_t l = big_len(ar.limb + soff[v], scap[v]);
+                    if (l > maxlen) maxlen = l;
+                }
+            }
+            int64_t off = arena_alloc(&ar, (size_t)maxlen + 1);
+            if (off < 0) { rc = -2; goto done; }
+            soff[w] = off;
+            scap[w] = maxlen + 1;
+            for (int32_t p = row_ptr[w]; p < row_ptr[w + 1]; ++p) {
+                int32_t v = col[p];
+                if (dist[v] >= 0 && dist[v] + (int64_t)weight[p] == dist[w])
+                    big_add(ar.limb + soff[w], scap[w], ar.limb + soff[v], big_len(ar.limb + soff[v], scap[v]));
+            }
+        }
+        /* ---- backward (Eq. 2) in reverse settle order ---- */
+        for (int32_t v = 0; v < n; ++v) delta[v] = 0.0;
+        for (int64_t q = nset - 1; q > 0; --q) {
+            int32_t w = order[q];
+            double mw;
+            int64_t ew;
+            oracle_big_to_scaled(ar.limb + soff[w], scap[w], &mw, &ew);
+            for (int32_t p = row_ptr[w]; p < row_ptr[w + 1]; ++p) {
+                int32_t v = col[p];
+                if (dist[v] >= 0 && dist[v] + (int64_t)weight[p] == dist[w])
+                    delta[v] += ratio(ar.limb + soff[v], scap[v], mw, ew) * (1.0 + delta[w]);
+            }
+        }
+        for (int32_t v = 0; v < n; ++v)
+            if (v != s) bc[v] += delta[v];
+        for (int64_t di = 0; di < n_dump; ++di) {
+            if (dump_idx[di] != si) continue;
+            for (int32_t v = 0; v < n; ++v) {
+                size_t at = (size_t)di * (size_t)n + (size_t)v;
+                int reach = dist[v] >= 0;
+                const uint64_t *sv = reach ? ar.limb + soff[v] : NULL;
+                int32_t lv = reach ? big_len(sv, scap[v]) : 0;
+                if (dump_dist) dump_dist[at] = (int32_t)dist[v];
+                if (dump_sigma) dump_sigma[at] = lv > 0 ? sv[0] : 0;
+                if (dump_ovf) dump_ovf[at] = (uint8_t)(lv > 1);
+                if (dump_delta) dump_delta[at] = delta[v];
+            }
+        }
+    }
+done:
+    free(dist); free(done_v); free(soff); free(scap); free(order); free(delta); free(heap);
+    free(ar.limb);
+    return rc;
+}

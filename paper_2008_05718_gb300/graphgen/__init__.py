@@ -58,6 +58,7 @@ def _load():
             lib.gg_grid.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, P(_CSR)]
             lib.gg_lcc.argtypes = [P(_CSR), P(_CSR), i32p]
             lib.gg_tri.argtypes = [ctypes.c_int32, ctypes.c_uint64, P(_CSR)]
+            lib.gg_weights.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_uint64, i32p]
             lib.gg_rgg.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P(_CSR)]
             lib.gg_mesh27.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P(_CSR)]
             lib.gg_sample_sources.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, i32p]
@@ -201,6 +202,37 @@ def mesh27(nx: int, ny: int = None, nz: int = None) -> Graph:
     if _load().gg_mesh27(int(nx), int(ny), int(nz), ctypes.byref(c)) != 0:
         raise ValueError("gg_mesh27 failed")
     return _take(c, f"mesh27_{nx}x{ny}x{nz}", {"dims": (nx, ny, nz)})
+
+
+def edge_weights(g: Graph, max_weight: int, seed: int) -> np.ndarray:
+    """Positive integer weights in [1, max_weight] aligned with g.col, one per
+    undirected edge (both CSR entries of an edge carry the same weight)."""
+    out = np.zeros(max(g.nnz, 1), np.int32)
+    rp = np.ascontiguousarray(g.row_ptr, dtype=np.int32)
+    cl = np.ascontiguousarray(g.col if g.nnz else np.zeros(1, np.int32), dtype=np.int32)
+    if _load().gg_weights(int(g.n), _i32p(rp), _i32p(cl), int(max_weight), int(seed), _i32p(out)) != 0:
+        raise ValueError("gg_weights: bad arguments")
+    return out[: g.nnz]
+
+
+def subdivide(g: Graph, weight: np.ndarray) -> Graph:
+    """Replace every edge {u, v} of weight c by a path of c unit edges through
+    c - 1 new vertices (numbered from g.n on); original vertices keep their ids."""
+    edges = []
+    nxt = g.n
+    for u in range(g.n):
+        for p in range(g.row_ptr[u], g.row_ptr[u + 1]):
+            v = int(g.col[p])
+            if u >= v:
+                continue
+            c = int(weight[p])
+            prev = u
+            for _ in range(c - 1):
+                edges.append((prev, nxt))
+                prev = nxt
+                nxt += 1
+            edges.append((prev, v))
+    return from_edges(nxt, edges, name=g.name + "_subdivided")
 
 
 def largest_cc(g: Graph) -> tuple[Graph, np.ndarray]:

@@ -46,7 +46,7 @@ static inline uint64_t gg_bounded(uint64_t r, uint64_t range) {
     return (uint64_t)(((__uint128_t)r * (__uint128_t)range) >> 64);
 }
 
-enum { ST_ER = 1, ST_RMAT = 2, ST_PERM = 3, ST_GRID = 4, ST_SRC = 5, ST_TRI = 6, ST_RGG = 7 };
+enum { ST_ER = 1, ST_RMAT = 2, ST_PERM = 3, ST_GRID = 4, ST_SRC = 5, ST_TRI = 6, ST_RGG = 7, ST_WEIGHT = 8 };
 
 typedef struct {
     int32_t n;
@@ -515,6 +515,22 @@ int gg_mesh27(int32_t nx, int32_t ny, int32_t nz, gg_csr *out) {
     free(eu);
     free(ev);
     return rc;
+}
+
+/* Edge weights for a symmetric CSR: the undirected edge {u, v} gets
+ * 1 + (value (min(u,v) * n + max(u,v)) of the weight stream, bounded to
+ * [0, max_weight)), so both of its entries carry the same weight. */
+int gg_weights(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t max_weight, uint64_t seed,
+               int32_t *out) {
+    if (n < 0 || max_weight < 1) return -1;
+    uint64_t key = gg_key(seed, ST_WEIGHT);
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t p = row_ptr[u]; p < row_ptr[u + 1]; ++p) {
+            int32_t v = col[p];
+            uint64_t a = (uint64_t)(u < v ? u : v), b = (uint64_t)(u < v ? v : u);
+            out[p] = 1 + (int32_t)gg_bounded(gg_at(key, a * (uint64_t)n + b), (uint64_t)max_weight);
+        }
+    return 0;
 }
 
 /* k distinct sources drawn uniformly from [0, n) (partial Fisher-Yates). */
