@@ -47,7 +47,12 @@ WORKLOADS = {
     "rgg20": "random geometric graph, 2^20 uniform points, expected degree 10, LCC, seed 7, 1024 uniform sources",
     "mesh100": "100x100x100 mesh, 27-point stencil (KKT-like banded pattern, average degree 25.5), "
                "4096 uniform sources (seed 8)",
+    "wrmat18": "the rmat18 graph and sources with integer edge weights uniform in [1, 16] (seed 216); "
+               "weighted shortest paths",
+    "wgrid1024": "the grid1024 graph and sources with integer edge weights uniform in [1, 16] (seed 217); "
+                 "weighted shortest paths",
 }
+WEIGHTED = {"wrmat18": ("rmat18", 16, 216), "wgrid1024": ("grid1024", 16, 217)}
 
 
 def parse():
@@ -74,11 +79,21 @@ def dist_env():
 
 
 def load_workload(name, rank):
+    """(graph, sources, edge weights or None)."""
     from paper_2008_05718_gb300 import graphgen as gg
-    g, S = gg.workload(name)
+    base, maxw, wseed = WEIGHTED.get(name, (name, 0, 0))
+    g, S = gg.workload(base)
+    w = gg.edge_weights(g, maxw, seed=wseed) if maxw else None
     if rank > 0:  # weak scaling: same count, another seeded sample
         S = gg.sample_sources(g.n, len(S), seed=10_000 + 97 * rank + len(S))
-    return g, S
+    return g, S, w
+
+
+def weighted_bytes_per_batch(n, nnz):
+    """Compulsory bytes of one weighted batch (64 sources): CSR and weights read
+    in the forward and the backward, dist (4 B) and sigma/psi (8 B) per
+    (vertex, lane) written and read in each phase, BC read and written."""
+    return 2 * (8 * nnz + 4 * (n + 1)) + 2 * 2 * 64 * n * (4 + 8) + 16 * n
 
 
 # ---- clocks -----------------------------------------------------------------
@@ -135,12 +150,15 @@ class ClockSampler:
 
 # ---- reference arm: the CPU oracle -------------------------------------------
 
-def cpu_oracle_gteps(g, S, sample):
+def cpu_oracle_gteps(g, S, sample, w=None):
     import oracle
     oracle.build()
     src = np.asarray(S[:sample], np.int32)
     t = time.perf_counter()
-    oracle.bc_graph(g, src)
+    if w is None:
+        oracle.bc_graph(g, src)
+    else:
+        oracle.bc_graph_weighted(g, w, src)
     dt = time.perf_counter() - t
     return len(src) * g.nnz / dt / 1e9, dt, len(src)
 
@@ -149,11 +167,11 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    g, S = load_workload(args.workload, 0)
+    g, S, w = load_workload(args.workload, 0)
     sample = max(1, min(args.cpu_sample // 4, len(S)))
     times = []
     for i in range(args.warmup + args.steps):
-        _, dt, k = cpu_oracle_gteps(g, S[i * sample % len(S):], sample)
+        _, dt, k = cpu_oracle_gteps(g, S[i * sample % len(S):], sample, w)
         if i >= args.warmup:
             times.append(dt)
     value = args.steps * sample * g.nnz / sum(times) / 1e9
@@ -212,11 +230,12 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     _build.build()
     gbbc.load()
-    g, S = load_workload(args.workload, rank)
+    g, S, wts = load_workload(args.workload, rank)
     k = len(S)
     stream = torch.cuda.current_stream(dev)
     rp = torch.from_numpy(g.row_ptr).to(dev)
     col = torch.from_numpy(g.col).to(dev)
+    wt = torch.from_numpy(wts).to(dev) if wts is not None else None
     src = torch.from_numpy(S).to(dev)
     out = torch.zeros(g.n, dtype=torch.float64, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -238,7 +257,12 @@ def run_ours(args):
             h.load_grouping(gweights)
         return h
 
-    bc = prepare(gbbc.BC.from_csr(g.n, rp, col, stream=stream, **opts))
+    def make(rp_, col_, wt_, **kw):
+        if wt_ is None:
+            return gbbc.BC.from_csr(g.n, rp_, col_, stream=stream, **kw)
+        return gbbc.BC.from_weighted(g.n, rp_, col_, wt_, stream=stream, **kw)
+
+    bc = prepare(make(rp, col, wt, **opts))
 
     def step():
         bc.reset()
@@ -277,26 +301,32 @@ def run_ours(args):
     col_h = torch.from_numpy(g.col).pin_memory()
     src_h = torch.from_numpy(S).pin_memory()
     out_h = torch.zeros(g.n, dtype=torch.float64).pin_memory()
+    wt_h = torch.from_numpy(wts).pin_memory() if wts is not None else None
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        with gbbc.BC.from_csr(g.n, rp_h, col_h, stream=stream, **opts) as h:
+        with make(rp_h, col_h, wt_h, **opts) as h:
             prepare(h)
             h.compute(src_h, stream=stream)
             h.read(out_h, stream=stream)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_val = k * g.nnz / e2e_s / 1e9 * world
-    h2d = (g.n + 1) * 4 + g.nnz * 4 + k * 4
+    h2d = (g.n + 1) * 4 + g.nnz * 4 + k * 4 + (g.nnz * 4 if wts is not None else 0)
     d2h = g.n * 8
 
     # ---- roofline of the dominant step kind (one traced step) ----
-    with gbbc.BC.from_csr(g.n, rp, col, stream=stream, flags=gbbc.GBBC_TRACE, **opts) as tb:
-        prepare(tb)
-        tb.compute(src, stream=stream)
-        tb.sync()
-        prof = tb.profile()
+    if wts is None:
+        with make(rp, col, None, flags=gbbc.GBBC_TRACE, **opts) as tb:
+            prepare(tb)
+            tb.compute(src, stream=stream)
+            tb.sync()
+            prof = tb.profile()
+    else:  # one launch of k_weighted_batches per step: the timed steps themselves
+        ms = 1e3 * total_s / args.steps
+        prof = {"weighted": {"ms": ms, "launches": 1,
+                             "bytes": weighted_bytes_per_batch(g.n, g.nnz) * ((k + 63) // 64)}}
     kind = max(prof, key=lambda x: prof[x]["ms"])
     p = prof[kind]
     peak, peak_src = measured_peaks()
@@ -313,7 +343,7 @@ def run_ours(args):
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        val, dt, ks = cpu_oracle_gteps(g, S, min(args.cpu_sample, k))
+        val, dt, ks = cpu_oracle_gteps(g, S, min(args.cpu_sample, k), wts)
         cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {ks} of the {k} sources, full graph; {dt:.1f} s on 1 core"}
 

@@ -315,6 +315,25 @@ gbbc_status bc_policy_eval(const float* params, const float* x, int64_t n, float
 gbbc_status bc_policy_load(gbbc_graph* g, const float* params, size_t bytes);
 
 /*
+ * bc_graph_create_weighted - a weighted graph: as bc_graph_create, plus
+ * weight[nnz] (host or device, copied), the positive integer length of each
+ * CSR entry's edge, in [1, GBBC_MAX_WEIGHT]; both entries of an edge must
+ * carry the same weight (checked when opt->validate is set).  Shortest paths
+ * are then those of least total weight (the SSSP case of the paper's forward
+ * phase, Sec. IV-C) and bc_compute adds Eq. 2's dependencies along them.
+ * The weighted path runs 64 sources per batch on one CTA each (batch_width 1
+ * is rejected; 32 runs as 64), ignores the direction policy, grouping and
+ * tracing, and keeps per-source state under GBBC_KEEP_STATE (distances as
+ * int32).  A shortest-path count reaching 2^64 fails bc_compute with
+ * GBBC_ERR_CAPACITY (no wide format here).  GBBC_ERR_INVALID also when
+ * max weight * (n - 1) may exceed the int32 distance range.
+ */
+#define GBBC_MAX_WEIGHT 64
+gbbc_status bc_graph_create_weighted(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+                                     const int32_t* weight, const gbbc_options* opt, void* stream,
+                                     gbbc_graph** out);
+
+/*
  * Learned source grouping.  A network of the same shape with K = 1 output
  * scores each source from six features (bc_source_features: log-scaled
  * degree of s, sum and maximum of its neighbours' degrees, and the size,

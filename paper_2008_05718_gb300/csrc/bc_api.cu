@@ -40,6 +40,11 @@ struct gbbc_graph {
     std::vector<long long> goff;     // graph vertex offsets (count + 1)
     u64* d_bc = nullptr;             // [2n] BC in 128-bit fixed point (units 2^-64)
     double* d_bc_out = nullptr;      // [n] staging for bc_read into host memory
+    int32_t* d_w = nullptr;          // edge weights (weighted graphs), aligned with d_col
+    int32_t max_w = 0;               // largest weight (0: unweighted)
+    WSlots wsl;                      // weighted path's per-CTA state
+    WBatch* d_wb = nullptr;
+    long long d_wb_cap = 0;
     std::vector<char> wide_graph;    // per graph: its batches start in the wide sigma format
     int max_clusters[4] = {0, 0, 0, 0};  // resident block-schedule clusters of 1, 2, 4, 8 CTAs
     int* d_gwide = nullptr;          // per graph: set by the block schedule when a batch went wide
@@ -695,6 +700,9 @@ gbbc_status grouping_scores(gbbc_graph* g, const std::vector<int32_t>& src, cons
 
 // Shared by bc_compute and bc_compute_multi: `gsrc` are whole-handle vertex
 // ids, `gid` their graph index.
+gbbc_status compute_weighted(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
+                             cudaStream_t st);
+
 gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
                          cudaStream_t st) {
     long long k = (long long)gsrc.size();
@@ -702,6 +710,7 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
         return fail(g, GBBC_ERR_STATE, "GBBC_POLICY_LEARNED needs weights (bc_policy_load)");
     CKS(alloc_keep(g, k, st));
     g->last_stream = st;
+    if (g->d_w) return compute_weighted(g, gsrc, gid, st);
     if (g->opt.batch_width == 1) {  // plain: one source at a time, list order
         CKS(alloc_plain(g));
         for (long long i = 0; i < k; ++i)
@@ -746,6 +755,125 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
         batches.push_back(b);
     }
     return dispatch(g, batches, st);
+}
+
+// ---- weighted graphs ----------------------------------------------------------
+
+double wslot_bytes(long long nslot, int L, int B) {
+    const long long levcap = 2 * nslot + 4096;
+    return (double)nslot * L * (4 + 8) + (double)B * nslot * L * 4 + (double)(nslot * L + L) * 4 +
+           (double)levcap * 4 + (double)(levcap + 1) * 8;
+}
+
+gbbc_status alloc_wslots(gbbc_graph* g, long long nslot, int L, int want) {
+    WSlots& S = g->wsl;
+    const int B = g->max_w + 1;
+    if (S.count >= want && S.nslot >= nslot && S.B == B && S.L == L) return GBBC_OK;
+    for (void* p : {(void*)S.dist, (void*)S.sp, (void*)S.blist, (void*)S.qv, (void*)S.levD, (void*)S.levOff})
+        dfree(g, p);
+    S = WSlots();
+    const long long qcap = nslot * L + L;
+    const long long levcap = 2 * nslot + 4096;
+    const long long bcap = nslot * L;  // a pair is listed at most once per bucket between its visits
+    const double per_slot = wslot_bytes(nslot, L, B);
+    size_t free_b = 0, total_b = 0;
+    CK(g, cudaMemGetInfo(&free_b, &total_b));
+    double budget = 0.5 * (double)free_b;
+    if (g->opt.mem_limit_bytes > 0) budget = std::min(budget, (double)g->opt.mem_limit_bytes - (double)g->bytes);
+    int count = (int)std::min<double>((double)want, std::floor(budget / per_slot));
+    if (count < 1) return fail(g, GBBC_ERR_OOM, "no room for one weighted-path slot (%.0f bytes)", per_slot);
+    const size_t c = (size_t)count, ns = (size_t)nslot;
+    S.nslot = nslot;
+    S.qcap = qcap;
+    S.levcap = levcap;
+    S.bcap = bcap;
+    S.count = count;
+    S.B = B;
+    S.L = L;
+    CKS(dalloc_t(g, &S.dist, c * ns * L));
+    CKS(dalloc_t(g, &S.sp, c * ns * L));
+    CKS(dalloc_t(g, &S.blist, c * (size_t)B * (size_t)bcap));
+    CKS(dalloc_t(g, &S.qv, c * (size_t)qcap));
+    CKS(dalloc_t(g, &S.levD, c * (size_t)levcap));
+    CKS(dalloc_t(g, &S.levOff, c * (size_t)(levcap + 1)));
+    return GBBC_OK;
+}
+
+// Weighted graphs: sources in list order (by graph), L per batch, one CTA per
+// batch, every batch in one launch (bc_weighted.cu).  L = ceil(k / nsm), at
+// most 64, so that the batches cover the SMs: work items are (vertex, lane)
+// pairs, so narrower batches lose nothing.
+gbbc_status compute_weighted(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
+                             cudaStream_t st) {
+    if (g->opt.batch_width == 1)
+        return fail(g, GBBC_ERR_INVALID, "weighted graphs have no one-source path (batch_width 1)");
+    const long long k = (long long)gsrc.size();
+    if (k == 0) return GBBC_OK;
+    std::vector<long long> order(k);
+    for (long long i = 0; i < k; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](long long a, long long b) { return gid[a] < gid[b]; });
+    long long nslot = 1;
+    for (long long i = 0; i < k; ++i)
+        nslot = std::max<long long>(nslot, g->goff[gid[i] + 1] - g->goff[gid[i]]);
+    // a slot's memory grows with L, so when fewer slots than SMs fit, wider
+    // batches do not raise the number of pairs in flight: L depends on k only
+    const int L = (int)std::max<long long>(1, std::min<long long>(kLanes, (k + g->nsm - 1) / g->nsm));
+    if ((double)nslot * L >= 2147483647.0)
+        return fail(g, GBBC_ERR_INVALID, "weighted path: n x lanes must stay below 2^31");
+    std::vector<WBatch> hb;
+    std::vector<int32_t> hsrc;
+    for (long long i = 0; i < k;) {
+        const int32_t gi = gid[order[i]];
+        WBatch b;
+        b.lo = (int32_t)g->goff[gi];
+        b.hi = (int32_t)g->goff[gi + 1];
+        b.first = order[i];
+        b.src_off = (long long)hsrc.size();
+        b.nsrc = 0;
+        b.pad = 0;
+        while (i < k && b.nsrc < L && gid[order[i]] == gi) {
+            if (g->k_dist && order[i] != b.first + b.nsrc)
+                return fail(g, GBBC_ERR_INVALID, "GBBC_KEEP_STATE needs the sources of each graph to be contiguous");
+            hsrc.push_back(gsrc[order[i]]);
+            ++b.nsrc;
+            ++i;
+        }
+        hb.push_back(b);
+    }
+    const int nb = (int)hb.size();
+    CKS(alloc_wslots(g, nslot, L, std::min(nb, g->nsm)));
+    if (g->d_wb_cap < nb) {
+        dfree(g, g->d_wb);
+        CKS(dalloc_t(g, &g->d_wb, (size_t)nb));
+        g->d_wb_cap = nb;
+    }
+    if (g->d_bsrc_cap < (long long)hsrc.size()) {
+        dfree(g, g->d_bsrc);
+        CKS(dalloc_t(g, &g->d_bsrc, hsrc.size()));
+        g->d_bsrc_cap = (long long)hsrc.size();
+    }
+    if (!g->d_next) CKS(dalloc_t(g, &g->d_next, 1));
+    if (!g->d_bstats) CKS(dalloc_t(g, &g->d_bstats, 4));
+    CK(g, cudaMemcpyAsync(g->d_wb, hb.data(), hb.size() * sizeof(WBatch), cudaMemcpyHostToDevice, st));
+    CK(g, cudaMemcpyAsync(g->d_bsrc, hsrc.data(), hsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(g, cudaMemsetAsync(g->d_next, 0, sizeof(unsigned), st));
+    CK(g, cudaMemsetAsync(g->d_bstats, 0, 4 * sizeof(unsigned long long), st));
+    Csr c{g->n, g->nnz, g->d_row_ptr, g->d_col};
+    CK(g, launch_weighted_batches(c, g->d_w, g->wsl, g->d_wb, nb, g->d_bsrc, g->d_next, g->d_bc, g->max_w, g->k_dist,
+                                  reinterpret_cast<u64*>(g->k_sigma), g->n, g->d_bstats, st));
+    g->stats.kernel_launches++;
+    unsigned long long hst[4];
+    CK(g, cudaMemcpyAsync(hst, g->d_bstats, sizeof(hst), cudaMemcpyDeviceToHost, st));
+    CK(g, cudaStreamSynchronize(st));
+    const unsigned err = (unsigned)(hst[3] & 0xffffffffull);
+    if (err & 1u) return fail(g, GBBC_ERR_CAPACITY, "weighted path: a shortest-path count reached 2^64");
+    if (err) return fail(g, GBBC_ERR_CAPACITY, "weighted path: capacity exceeded (flags %u)", err);
+    if ((int)hst[0] != nb) return fail(g, GBBC_ERR_CUDA, "weighted path ran %llu of %d batches", hst[0], nb);
+    g->stats.batches += nb;
+    g->stats.sources += k;
+    g->stats.levels_fwd += (long long)hst[1];
+    g->stats.levels_push += (long long)hst[1];
+    return GBBC_OK;
 }
 
 // ---- block-per-batch schedule ----------------------------------------------
@@ -1142,6 +1270,59 @@ gbbc_status bc_graph_create(int32_t n, int64_t nnz, const int32_t* row_ptr, cons
         return r;
     }
     *out = g;
+    return GBBC_OK;
+}
+
+gbbc_status bc_graph_create_weighted(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+                                     const int32_t* weight, const gbbc_options* opt, void* stream,
+                                     gbbc_graph** out) {
+    if (!out) return GBBC_ERR_INVALID;
+    *out = nullptr;
+    if (nnz > 0 && !weight) return GBBC_ERR_INVALID;
+    gbbc_status r = bc_graph_create(n, nnz, row_ptr, col, opt, stream, out);
+    if (r != GBBC_OK) return r;
+    gbbc_graph* g = *out;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> w;
+    r = to_host(g, w, weight, (size_t)nnz, st);
+    int32_t maxw = 1;
+    if (r == GBBC_OK) {
+        for (long long p = 0; p < nnz; ++p) {
+            if (w[p] < 1 || w[p] > kMaxWeight) {
+                r = fail(g, GBBC_ERR_INVALID, "weight %d at entry %lld outside [1, %d]", w[p], p, kMaxWeight);
+                break;
+            }
+            maxw = std::max(maxw, w[p]);
+        }
+    }
+    if (r == GBBC_OK && (long long)maxw * std::max<long long>(n - 1, 0) > 0x7fffffffLL - kMaxWeight)
+        r = fail(g, GBBC_ERR_INVALID, "max weight %d times n - 1 may exceed the int32 distance range", maxw);
+    if (r == GBBC_OK && g->opt.validate) {  // symmetric weights: w(u, v) == w(v, u)
+        std::vector<int32_t> hc((size_t)nnz);
+        if (nnz > 0 && cudaMemcpy(hc.data(), g->d_col, (size_t)nnz * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+                           cudaSuccess)
+            r = fail(g, GBBC_ERR_CUDA, "copy of col failed");
+        for (int32_t u = 0; u < n && r == GBBC_OK; ++u)
+            for (int32_t p = g->h_row_ptr[u]; p < g->h_row_ptr[u + 1]; ++p) {
+                const int32_t v = hc[p];
+                const int32_t* b = hc.data() + g->h_row_ptr[v];
+                const int32_t* e = hc.data() + g->h_row_ptr[v + 1];
+                const int32_t* q = std::lower_bound(b, e, u);  // rows are sorted (checked by validation)
+                if (q == e || *q != u || w[q - hc.data()] != w[p]) {
+                    r = fail(g, GBBC_ERR_INVALID, "weight of edge (%d, %d) differs from (%d, %d)", u, v, v, u);
+                    break;
+                }
+            }
+    }
+    if (r == GBBC_OK) r = dalloc_t(g, &g->d_w, (size_t)std::max<int64_t>(nnz, 1));
+    if (r == GBBC_OK) r = to_device(g, g->d_w, w.data(), (size_t)nnz * sizeof(int32_t), st);
+    if (r == GBBC_OK && cudaStreamSynchronize(st) != cudaSuccess) r = fail(g, GBBC_ERR_CUDA, "sync failed");
+    if (r != GBBC_OK) {
+        release_failed(g, r);
+        *out = nullptr;
+        return r;
+    }
+    g->max_w = maxw;
     return GBBC_OK;
 }
 

@@ -168,6 +168,40 @@ void launch_keep_sigma(const Slot& s, int32_t lo, int32_t hi, uint64_t* sigma, u
 void launch_undo(const Slot& s, long long q_lo, long long q_hi, cudaStream_t st);
 // Block-per-batch persistent kernel over `nb` batches; stats[0..3]: batches,
 // forward levels, bottom-up levels, wide reruns (device, accumulated).
+// ---- weighted graphs (bc_weighted.cu) ----
+constexpr int kWThreads = 512;   // one CTA per batch
+constexpr int kMaxWeight = 64;   // weights in [1, kMaxWeight]
+constexpr int kMaxBuckets = kMaxWeight + 1;
+constexpr int kWHeavy = 64;      // rows longer than this are scanned by a whole warp
+
+struct WBatch {
+    int32_t lo, hi, nsrc, pad;
+    long long first;    // position of the batch's first source in the call's list
+    long long src_off;  // first source of the batch in the uploaded source array
+};
+
+// Per-CTA state of the weighted path: `count` slots of nslot vertices with L
+// lanes (sources) each; a (vertex, lane) pair has id v * L + lane.
+struct WSlots {
+    long long nslot = 0, qcap = 0, levcap = 0, bcap = 0;
+    int count = 0, B = 0, L = 0;  // slots; buckets (max weight + 1); lanes per batch
+    int32_t* dist = nullptr;      // [count][nslot][L]
+    u64* sp = nullptr;            // [count][nslot][L] sigma, then psi
+    uint32_t* blist = nullptr;    // [count][B][bcap] pair ids pending per bucket
+    uint32_t* qv = nullptr;       // [count][qcap] settled pairs in distance order
+    int32_t* levD = nullptr;      // [count][levcap] distance of each settle step
+    long long* levOff = nullptr;  // [count][levcap + 1] queue offset of each step
+};
+
+// Every batch of a weighted graph (weights in [1, W]); stats[0] += batches
+// done, stats[1] += settle steps, low word of stats[3] |= error bits (1: a
+// path count reached 2^64, 2: too many distinct distances, 4: queue full,
+// 8: a bucket list full).  k_dist/k_sigma (may be null) receive the
+// per-source state, rows by source position, n_total columns.
+cudaError_t launch_weighted_batches(const Csr& g, const int32_t* wt, const WSlots& S, const WBatch* batches, int nb,
+                                    const int32_t* srcs, unsigned* next, u64* bc, int W, int32_t* k_dist,
+                                    u64* k_sigma, long long n_total, unsigned long long* stats, cudaStream_t st);
+
 // Clusters of csize CTAs of k_block_batches that fit on the device at once
 // (0 if the query fails).
 int block_max_clusters(int csize);

@@ -27,13 +27,14 @@ GBBC_TRACE = 2
 GBBC_TRACE_BOTH = 4
 
 # every symbol include/gbbc.h declares
-EXPORTS = ("bc_options_init", "bc_graph_create", "bc_graph_create_multi", "bc_compute", "bc_compute_multi",
+EXPORTS = ("bc_options_init", "bc_graph_create", "bc_graph_create_multi", "bc_graph_create_weighted", "bc_compute", "bc_compute_multi",
            "bc_read", "bc_read_source_state", "bc_reset", "bc_sync", "bc_graph_destroy", "bc_status_string",
            "bc_last_error_detail", "bc_get_stats", "bc_get_trace", "bc_clear_trace", "bc_get_profile",
            "bc_compute_noalloc", "bc_mlp_param_count", "bc_mlp_forward", "bc_mlp_loss_grad", "bc_mlp_adam_step",
            "bc_mlp_train", "bc_policy_eval", "bc_policy_load", "bc_read_fixed", "bc_source_features",
            "bc_grouping_load", "bc_grouping_scores")
 NOALLOC_MAX_VERTICES = 16384
+MAX_WEIGHT = 64  # GBBC_MAX_WEIGHT
 
 
 class gbbc_options(ctypes.Structure):
@@ -92,6 +93,7 @@ def load():
         sig = {
             "bc_options_init": (None, [P(gbbc_options)]),
             "bc_graph_create": (ctypes.c_int, [i32, i64, vp, vp, P(gbbc_options), vp, P(vp)]),
+            "bc_graph_create_weighted": (ctypes.c_int, [i32, i64, vp, vp, vp, P(gbbc_options), vp, P(vp)]),
             "bc_graph_create_multi": (ctypes.c_int, [i32, vp, vp, vp, vp, P(gbbc_options), vp, P(vp)]),
             "bc_compute": (ctypes.c_int, [vp, vp, i64, vp]),
             "bc_compute_multi": (ctypes.c_int, [vp, vp, vp, i64, vp]),
@@ -206,6 +208,18 @@ def bc_graph_create(n, nnz, row_ptr, col, opt=None, stream=None):
     h = ctypes.c_void_p()
     st = load().bc_graph_create(int(n), int(nnz), rp, cl, ctypes.byref(opt) if opt is not None else None,
                                 _stream(stream), ctypes.byref(h))
+    _check(st)
+    return h
+
+
+def bc_graph_create_weighted(n, nnz, row_ptr, col, weight, opt=None, stream=None):
+    rp, k1 = _ptr(_as_i32(row_ptr))
+    cl, k2 = _ptr(_as_i32(col))
+    wt, k3 = _ptr(_as_i32(weight))
+    h = ctypes.c_void_p()
+    st = load().bc_graph_create_weighted(int(n), int(nnz), rp, cl, wt,
+                                         ctypes.byref(opt) if opt is not None else None, _stream(stream),
+                                         ctypes.byref(h))
     _check(st)
     return h
 
@@ -469,6 +483,12 @@ class BC:
     @classmethod
     def from_graph(cls, g, stream=None, **opts):
         return cls.from_csr(g.n, g.row_ptr, g.col, stream=stream, **opts)
+
+    @classmethod
+    def from_weighted(cls, n, row_ptr, col, weight, stream=None, **opts):
+        """A weighted graph: weight[p] is the length of CSR entry p's edge."""
+        nnz = int(row_ptr[-1]) if len(row_ptr) else 0
+        return cls(bc_graph_create_weighted(n, nnz, row_ptr, col, weight, options(**opts), stream), n)
 
     @classmethod
     def from_graphs(cls, graphs, stream=None, **opts):

@@ -1,0 +1,121 @@
+"""The weighted path on the GPU against the weighted oracle: dist and sigma
+bit-exact (kept per-source state), BC within 1e-12 relative; unit weights
+give the unweighted path's exact bits; overflow and bad weights are errors."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_05718_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+def assert_bc_close(got, want):
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-15), np.max(np.abs(got - want))
+
+
+def run_w(gb, g, w, S, keep=(), **opts):
+    flags = gb.GBBC_KEEP_STATE if keep else 0
+    with gb.BC.from_weighted(g.n, g.row_ptr, g.col, w, flags=flags, **opts) as bc:
+        bc.compute(np.asarray(S, np.int32))
+        out = bc.read()
+        fixed = bc.read_fixed()
+        states = {i: bc.source_state(i) for i in keep}
+        stats = bc.stats()
+    return out, fixed, states, stats
+
+
+def check_w(gb, g, w, S, keep=(), **opts):
+    want, ost = oracle.bc_graph_weighted(g, w, S, dump=keep)
+    got, fixed, st, stats = run_w(gb, g, w, S, keep, **opts)
+    assert_bc_close(got, want)
+    for i in keep:
+        d, s, o = st[i]
+        assert np.array_equal(d, ost[i].dist), f"dist of source #{i}"
+        assert np.array_equal(s, ost[i].sigma), f"sigma of source #{i}"
+        assert not o.any()
+    return got, fixed, stats
+
+
+CASES = [
+    ("rmat10_w4", lambda: gg.rmat(10, 16, seed=201), 4, 150),
+    ("grid40_w8", lambda: gg.grid(40, "0.05", seed=202), 8, 130),
+    ("er800_w16", lambda: gg.er(800, "8/799", seed=203), 16, 200),
+    ("tri30_w64", lambda: gg.tri(30, seed=204), 64, 100),
+    ("rgg_w3", lambda: gg.rgg(2000, 10.0, seed=205), 3, 64),
+    ("er800_all_w16", lambda: gg.er(800, "8/799", seed=208), 16, 800),  # 6 lanes per batch
+    ("rmat12_w2", lambda: gg.rmat(12, 16, seed=209), 2, 4000),  # 27 lanes per batch, many ties
+]
+
+
+@pytest.mark.parametrize("name,make,maxw,k", CASES, ids=[c[0] for c in CASES])
+def test_weighted_parity(gb, name, make, maxw, k):
+    g = make()
+    w = gg.edge_weights(g, maxw, seed=206)
+    S = gg.sample_sources(g.n, min(k, g.n), seed=207)
+    _, fixed, stats = check_w(gb, g, w, S, keep=(0, len(S) - 1))
+    lanes = max(1, min(64, -(-len(S) // 152)))
+    assert stats["batches"] >= (len(S) + lanes - 1) // lanes
+    # rerun: the same bits
+    _, fixed2, _, _ = run_w(gb, g, w, S)
+    assert np.array_equal(fixed, fixed2)
+
+
+def test_weighted_hand_example(gb):
+    g = gg.from_edges(4, [(0, 1), (1, 3), (0, 2), (2, 3)])
+    u = np.repeat(np.arange(4), np.diff(g.row_ptr))
+    wt = {(0, 1): 1, (1, 3): 1, (0, 2): 1, (2, 3): 2}
+    w = np.array([wt[(min(a, b), max(a, b))] for a, b in zip(u, g.col)], np.int32)
+    got, _, _, _ = run_w(gb, g, w, np.arange(4))
+    assert np.array_equal(got, [2.0, 2.0, 0.0, 0.0])
+
+
+@pytest.mark.parametrize("make", [lambda: gg.rmat(11, 16, seed=210), lambda: gg.grid(24, "0.05", seed=211),
+                                  lambda: gg.star(30)])
+def test_unit_weights_give_the_unweighted_bits(gb, make):
+    g = make()
+    S = gg.sample_sources(g.n, min(200, g.n), seed=212)
+    _, fixed, _, _ = run_w(gb, g, np.ones(g.nnz, np.int32), S)
+    with gb.BC.from_graph(g) as bc:
+        bc.compute(S)
+        assert np.array_equal(bc.read_fixed(), fixed)
+
+
+def test_weighted_edge_cases(gb):
+    # isolated vertices, duplicated sources, a source repeated within a batch
+    g = gg.from_edges(8, [(0, 1), (1, 2), (2, 3), (5, 6)])
+    u = np.repeat(np.arange(8), np.diff(g.row_ptr))
+    w = np.array([1 + (int(a) + int(b)) % 3 for a, b in zip(u, g.col)], np.int32)
+    S = [0, 0, 4, 5, 3, 7, 2, 2]
+    check_w(gb, g, w, S, keep=(0, 1, 2))
+    # more than one batch, ragged tail, on a multi-level graph
+    h = gg.grid(20, "0.1", seed=213)
+    wh = gg.edge_weights(h, 5, seed=214)
+    check_w(gb, h, wh, gg.sample_sources(h.n, 199, seed=215), keep=(64, 198))
+
+
+def test_weighted_overflow_and_invalid_weights(gb):
+    g = gg.diamond_chain(70)  # 2^70 shortest paths at unit weights
+    with gb.BC.from_weighted(g.n, g.row_ptr, g.col, np.ones(g.nnz, np.int32)) as bc:
+        with pytest.raises(gb.GbbcError) as e:
+            bc.compute([0])
+        assert e.value.status == gb.GBBC_ERR_CAPACITY
+    h = gg.path(5)
+    for bad in (np.zeros(h.nnz, np.int32), np.full(h.nnz, gb.MAX_WEIGHT + 1, np.int32)):
+        with pytest.raises(gb.GbbcError) as e:
+            gb.BC.from_weighted(h.n, h.row_ptr, h.col, bad)
+        assert e.value.status == gb.GBBC_ERR_INVALID
+    asym = np.arange(1, h.nnz + 1, dtype=np.int32)
+    with pytest.raises(gb.GbbcError) as e:
+        gb.BC.from_weighted(h.n, h.row_ptr, h.col, asym, validate=True)
+    assert e.value.status == gb.GBBC_ERR_INVALID
+    with gb.BC.from_weighted(h.n, h.row_ptr, h.col, np.ones(h.nnz, np.int32), batch_width=1) as bc:
+        with pytest.raises(gb.GbbcError) as e:
+            bc.compute([0])
+        assert e.value.status == gb.GBBC_ERR_INVALID
+
+
+def test_weighted_full_size_sampled(gb):
+    g, S = gg.workload("rmat18")
+    w = gg.edge_weights(g, 16, seed=216)
+    check_w(gb, g, w, S[:64], keep=(0, 63))
