@@ -89,11 +89,13 @@ def load_workload(name, rank):
     return g, S, w
 
 
-def weighted_bytes_per_batch(n, nnz):
-    """Compulsory bytes of one weighted batch (64 sources): CSR and weights read
-    in the forward and the backward, dist (4 B) and sigma/psi (8 B) per
-    (vertex, lane) written and read in each phase, BC read and written."""
-    return 2 * (8 * nnz + 4 * (n + 1)) + 2 * 2 * 64 * n * (4 + 8) + 16 * n
+def pair_bytes_per_step(n, nnz, k, nb, weighted):
+    """Compulsory bytes of one call of the pair-granular kernel (k sources in
+    nb batches): per batch the CSR (and weights) read in the forward and the
+    backward and BC read and written; per (vertex, source) pair dist (4 B)
+    and sigma/psi (8 B) written and read in each phase."""
+    csr = (8 if weighted else 4) * nnz + 4 * (n + 1)
+    return nb * (2 * csr + 16 * n) + 2 * 2 * k * n * (4 + 8)
 
 
 # ---- clocks -----------------------------------------------------------------
@@ -317,16 +319,18 @@ def run_ours(args):
     d2h = g.n * 8
 
     # ---- roofline of the dominant step kind (one traced step) ----
-    if wts is None:
+    st_all = bc.stats()
+    if wts is None and st_all["schedule"] != 3:
         with make(rp, col, None, flags=gbbc.GBBC_TRACE, **opts) as tb:
             prepare(tb)
             tb.compute(src, stream=stream)
             tb.sync()
             prof = tb.profile()
-    else:  # one launch of k_weighted_batches per step: the timed steps themselves
+    else:  # one launch of the pair-granular kernel per step: the timed steps themselves
         ms = 1e3 * total_s / args.steps
-        prof = {"weighted": {"ms": ms, "launches": 1,
-                             "bytes": weighted_bytes_per_batch(g.n, g.nnz) * ((k + 63) // 64)}}
+        nb = st_all["batches"] // max(1, args.warmup + args.steps)
+        prof = {"pair": {"ms": ms, "launches": 1,
+                         "bytes": pair_bytes_per_step(g.n, g.nnz, k, nb, wts is not None)}}
     kind = max(prof, key=lambda x: prof[x]["ms"])
     p = prof[kind]
     peak, peak_src = measured_peaks()
@@ -355,6 +359,7 @@ def run_ours(args):
                            "n": g.n, "nnz": g.nnz, "batch_width": args.width,
                            "policy": args.policy + (" (learned, shipped weights)" if weights is not None else ""),
                            "source_grouping": "learned (shipped weights)" if gweights is not None else "list order",
+                           "schedule": ["auto", "grid", "block", "pair"][st_all["schedule"]],
                            "l2": "flushed between timed steps (512 MiB device write)"},
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,

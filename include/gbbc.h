@@ -91,18 +91,29 @@ typedef struct gbbc_options {
 
 /* How batches are mapped to the GPU. */
 enum gbbc_schedule {
-    GBBC_SCHEDULE_AUTO = 0,  /* batches of graphs above 65,536 vertices with
-                                average degree above 6 run grid; for the others
-                                the first call times its first batches in both
-                                modes (results kept) and the faster mode is
-                                kept for the handle; results are identical
-                                either way */
+    GBBC_SCHEDULE_AUTO = 0,  /* one graph above 65,536 vertices with average
+                                degree at most 12 and a BFS eccentricity of at
+                                least 64 (from a vertex of the largest row)
+                                runs pair; batches of other graphs above 65,536
+                                vertices with average degree above 6 run grid;
+                                for the rest, block when the batches fill the
+                                GPU, else the first call times some batches in
+                                both modes (results kept) and the faster mode
+                                is kept for the handle */
     GBBC_SCHEDULE_GRID = 1,  /* one batch at a time on the whole GPU, a kernel
                                 per level step, host read-back per level */
-    GBBC_SCHEDULE_BLOCK = 2  /* one thread-block cluster (1 to 8 blocks) per
+    GBBC_SCHEDULE_BLOCK = 2, /* one thread-block cluster (1 to 8 blocks) per
                                 batch, many batches at once, one persistent
                                 launch per call; the level loop runs on the
                                 device (cluster barriers only) */
+    GBBC_SCHEDULE_PAIR = 3   /* the weighted graphs' kernel with all weights
+                                1: one block per batch of ceil(k / SMs)
+                                sources, work items (vertex, source) pairs,
+                                for graphs whose sources rarely share a BFS
+                                level (high diameter); one launch per call.
+                                BC agrees with the other schedules to
+                                rounding, bit for bit while path counts stay
+                                below 2^64 */
 };
 
 /* Fill *opt with defaults (auto width, auto policy, no validation). */

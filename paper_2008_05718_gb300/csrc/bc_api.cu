@@ -47,6 +47,7 @@ struct gbbc_graph {
     long long d_wb_cap = 0;
     std::vector<char> wide_graph;    // per graph: its batches start in the wide sigma format
     int max_clusters[4] = {0, 0, 0, 0};  // resident block-schedule clusters of 1, 2, 4, 8 CTAs
+    int pair_auto = -1;              // GBBC_SCHEDULE_AUTO takes the pair schedule: -1 not yet decided
     int* d_gwide = nullptr;          // per graph: set by the block schedule when a batch went wide
     Slot slot;
     bool slot_ready = false;
@@ -217,7 +218,7 @@ gbbc_status read_options(gbbc_graph* g, const gbbc_options* opt) {
     if (o.policy < GBBC_POLICY_AUTO || o.policy > GBBC_POLICY_PULL)
         return fail(g, GBBC_ERR_INVALID, "unknown policy %d", o.policy);
     if (o.heavy_degree < 0) return fail(g, GBBC_ERR_INVALID, "heavy_degree must be >= 0");
-    if (o.schedule < GBBC_SCHEDULE_AUTO || o.schedule > GBBC_SCHEDULE_BLOCK)
+    if (o.schedule < GBBC_SCHEDULE_AUTO || o.schedule > GBBC_SCHEDULE_PAIR)
         return fail(g, GBBC_ERR_INVALID, "unknown schedule %d", o.schedule);
     if (g->opt.heavy_degree == 0) g->opt.heavy_degree = 1024;
     if (g->opt.heavy_degree < 32) g->opt.heavy_degree = 32;
@@ -703,6 +704,45 @@ gbbc_status grouping_scores(gbbc_graph* g, const std::vector<int32_t>& src, cons
 gbbc_status compute_weighted(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
                              cudaStream_t st);
 
+// Under GBBC_SCHEDULE_AUTO, one large sparse graph of high diameter runs in
+// the pair schedule: its sources rarely share a BFS level, so 64-lane rows
+// are mostly idle (measured: 1024^2 triangulation 1.54x, 2^20-point random
+// geometric graph 1.52x, 1024^2 grid 1.13x faster; the 100^3 mesh, degree 26,
+// and small or low-diameter graphs are faster in the bitset schedules).  The
+// test: one graph above 65,536 vertices, average degree at most 12, and a
+// BFS eccentricity of at least 64 from a vertex of the largest row (host BFS
+// over a host copy of the columns, once per handle).
+bool pair_auto(gbbc_graph* g) {
+    if (g->pair_auto >= 0) return g->pair_auto == 1;
+    g->pair_auto = 0;
+    const long long n = g->n;
+    if (g->goff.size() != 2 || n <= 65536 || (double)g->nnz > 12.0 * (double)n) return false;
+    std::vector<int32_t> col((size_t)g->nnz);
+    if (cudaMemcpy(col.data(), g->d_col, (size_t)g->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int32_t s = 0;
+    for (int32_t v = 1; v < (int32_t)n; ++v)
+        if (g->h_row_ptr[v + 1] - g->h_row_ptr[v] > g->h_row_ptr[s + 1] - g->h_row_ptr[s]) s = v;
+    std::vector<int32_t> dist((size_t)n, -1), queue;
+    queue.reserve((size_t)n);
+    dist[s] = 0;
+    queue.push_back(s);
+    int32_t ecc = 0;
+    for (size_t h = 0; h < queue.size(); ++h) {
+        const int32_t v = queue[h];
+        for (int32_t p = g->h_row_ptr[v]; p < g->h_row_ptr[v + 1]; ++p)
+            if (dist[col[p]] < 0) {
+                dist[col[p]] = dist[v] + 1;
+                ecc = std::max(ecc, dist[v] + 1);
+                queue.push_back(col[p]);
+            }
+    }
+    g->pair_auto = ecc >= 64 ? 1 : 0;
+    return g->pair_auto == 1;
+}
+
 gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
                          cudaStream_t st) {
     long long k = (long long)gsrc.size();
@@ -710,7 +750,10 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
         return fail(g, GBBC_ERR_STATE, "GBBC_POLICY_LEARNED needs weights (bc_policy_load)");
     CKS(alloc_keep(g, k, st));
     g->last_stream = st;
-    if (g->d_w) return compute_weighted(g, gsrc, gid, st);
+    if (g->d_w || g->opt.schedule == GBBC_SCHEDULE_PAIR ||
+        (g->opt.schedule == GBBC_SCHEDULE_AUTO && g->opt.batch_width != 1 && !(g->opt.flags & GBBC_TRACE) &&
+         pair_auto(g)))
+        return compute_weighted(g, gsrc, gid, st);
     if (g->opt.batch_width == 1) {  // plain: one source at a time, list order
         CKS(alloc_plain(g));
         for (long long i = 0; i < k; ++i)
@@ -761,15 +804,15 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
 
 double wslot_bytes(long long nslot, int L, int B) {
     const long long levcap = 2 * nslot + 4096;
-    return (double)nslot * L * (4 + 8) + (double)B * nslot * L * 4 + (double)(nslot * L + L) * 4 +
+    return (double)nslot * L * (4 + 8 + 8 + 4 + 1) + (double)B * nslot * L * 4 + (double)(nslot * L + L) * 4 +
            (double)levcap * 4 + (double)(levcap + 1) * 8;
 }
 
-gbbc_status alloc_wslots(gbbc_graph* g, long long nslot, int L, int want) {
+gbbc_status alloc_wslots(gbbc_graph* g, long long nslot, int L, int B, int want) {
     WSlots& S = g->wsl;
-    const int B = g->max_w + 1;
     if (S.count >= want && S.nslot >= nslot && S.B == B && S.L == L) return GBBC_OK;
-    for (void* p : {(void*)S.dist, (void*)S.sp, (void*)S.blist, (void*)S.qv, (void*)S.levD, (void*)S.levOff})
+    for (void* p : {(void*)S.dist, (void*)S.sp, (void*)S.blist, (void*)S.qv, (void*)S.levD, (void*)S.levOff,
+                    (void*)S.sN, (void*)S.sX, (void*)S.wf})
         dfree(g, p);
     S = WSlots();
     const long long qcap = nslot * L + L;
@@ -796,17 +839,22 @@ gbbc_status alloc_wslots(gbbc_graph* g, long long nslot, int L, int want) {
     CKS(dalloc_t(g, &S.qv, c * (size_t)qcap));
     CKS(dalloc_t(g, &S.levD, c * (size_t)levcap));
     CKS(dalloc_t(g, &S.levOff, c * (size_t)(levcap + 1)));
+    CKS(dalloc_t(g, &S.sN, c * ns * L));
+    CKS(dalloc_t(g, &S.sX, c * ns * L));
+    CKS(dalloc_t(g, &S.wf, c * ns * L));
     return GBBC_OK;
 }
 
-// Weighted graphs: sources in list order (by graph), L per batch, one CTA per
-// batch, every batch in one launch (bc_weighted.cu).  L = ceil(k / nsm), at
-// most 64, so that the batches cover the SMs: work items are (vertex, lane)
-// pairs, so narrower batches lose nothing.
+// Pair-granular kernel (bc_weighted.cu), for weighted graphs and for
+// unweighted ones under GBBC_SCHEDULE_PAIR (all weights 1): sources in list
+// order (by graph), L per batch, one CTA per batch, every batch in one
+// launch.  L = ceil(k / nsm), at most 64, so that the batches cover the SMs:
+// work items are (vertex, lane) pairs, so narrower batches lose nothing.
 gbbc_status compute_weighted(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
                              cudaStream_t st) {
     if (g->opt.batch_width == 1)
-        return fail(g, GBBC_ERR_INVALID, "weighted graphs have no one-source path (batch_width 1)");
+        return fail(g, GBBC_ERR_INVALID, "the pair-granular path has no one-source form (batch_width 1)");
+    const int W = g->d_w ? g->max_w : 1;
     const long long k = (long long)gsrc.size();
     if (k == 0) return GBBC_OK;
     std::vector<long long> order(k);
@@ -830,6 +878,8 @@ gbbc_status compute_weighted(gbbc_graph* g, const std::vector<int32_t>& gsrc, co
         b.first = order[i];
         b.src_off = (long long)hsrc.size();
         b.nsrc = 0;
+        b.gi = gi;
+        b.wide = g->wide_graph[gi];
         b.pad = 0;
         while (i < k && b.nsrc < L && gid[order[i]] == gi) {
             if (g->k_dist && order[i] != b.first + b.nsrc)
@@ -841,7 +891,10 @@ gbbc_status compute_weighted(gbbc_graph* g, const std::vector<int32_t>& gsrc, co
         hb.push_back(b);
     }
     const int nb = (int)hb.size();
-    CKS(alloc_wslots(g, nslot, L, std::min(nb, g->nsm)));
+    CKS(alloc_wslots(g, nslot, L, W + 1, std::min(nb, g->nsm)));
+    const size_t ngraphs = g->wide_graph.size();
+    if (!g->d_gwide) CKS(dalloc_t(g, &g->d_gwide, ngraphs));
+    CK(g, cudaMemsetAsync(g->d_gwide, 0, ngraphs * sizeof(int), st));
     if (g->d_wb_cap < nb) {
         dfree(g, g->d_wb);
         CKS(dalloc_t(g, &g->d_wb, (size_t)nb));
@@ -859,20 +912,26 @@ gbbc_status compute_weighted(gbbc_graph* g, const std::vector<int32_t>& gsrc, co
     CK(g, cudaMemsetAsync(g->d_next, 0, sizeof(unsigned), st));
     CK(g, cudaMemsetAsync(g->d_bstats, 0, 4 * sizeof(unsigned long long), st));
     Csr c{g->n, g->nnz, g->d_row_ptr, g->d_col};
-    CK(g, launch_weighted_batches(c, g->d_w, g->wsl, g->d_wb, nb, g->d_bsrc, g->d_next, g->d_bc, g->max_w, g->k_dist,
-                                  reinterpret_cast<u64*>(g->k_sigma), g->n, g->d_bstats, st));
+    CK(g, launch_weighted_batches(c, g->d_w, g->wsl, g->d_wb, nb, g->d_bsrc, g->d_next, g->d_bc, W, g->k_dist,
+                                  reinterpret_cast<u64*>(g->k_sigma), g->k_ovf, g->n, g->d_gwide, g->d_bstats, st));
     g->stats.kernel_launches++;
     unsigned long long hst[4];
+    std::vector<int> gw(ngraphs);
     CK(g, cudaMemcpyAsync(hst, g->d_bstats, sizeof(hst), cudaMemcpyDeviceToHost, st));
+    CK(g, cudaMemcpyAsync(gw.data(), g->d_gwide, ngraphs * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(g, cudaStreamSynchronize(st));
     const unsigned err = (unsigned)(hst[3] & 0xffffffffull);
-    if (err & 1u) return fail(g, GBBC_ERR_CAPACITY, "weighted path: a shortest-path count reached 2^64");
-    if (err) return fail(g, GBBC_ERR_CAPACITY, "weighted path: capacity exceeded (flags %u)", err);
-    if ((int)hst[0] != nb) return fail(g, GBBC_ERR_CUDA, "weighted path ran %llu of %d batches", hst[0], nb);
+    if (err) return fail(g, GBBC_ERR_CAPACITY, "pair-granular path: capacity exceeded (flags %u)", err);
+    if ((int)hst[0] != nb) return fail(g, GBBC_ERR_CUDA, "pair-granular path ran %llu of %d batches", hst[0], nb);
     g->stats.batches += nb;
     g->stats.sources += k;
     g->stats.levels_fwd += (long long)hst[1];
     g->stats.levels_push += (long long)hst[1];
+    for (const WBatch& b : hb) g->stats.wide_batches += b.wide;
+    g->stats.wide_batches += (long long)hst[2];
+    for (size_t i = 0; i < ngraphs; ++i)
+        if (gw[i]) g->wide_graph[i] = 1;  // later batches of this graph start wide
+    g->stats.schedule = GBBC_SCHEDULE_PAIR;
     return GBBC_OK;
 }
 

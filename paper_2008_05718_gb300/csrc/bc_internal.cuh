@@ -175,7 +175,8 @@ constexpr int kMaxBuckets = kMaxWeight + 1;
 constexpr int kWHeavy = 64;      // rows longer than this are scanned by a whole warp
 
 struct WBatch {
-    int32_t lo, hi, nsrc, pad;
+    int32_t lo, hi, nsrc, gi;
+    int32_t wide, pad;  // wide = 1: start in the wide sigma format
     long long first;    // position of the batch's first source in the call's list
     long long src_off;  // first source of the batch in the uploaded source array
 };
@@ -191,16 +192,23 @@ struct WSlots {
     uint32_t* qv = nullptr;       // [count][qcap] settled pairs in distance order
     int32_t* levD = nullptr;      // [count][levcap] distance of each settle step
     long long* levOff = nullptr;  // [count][levcap + 1] queue offset of each step
+    u64* sN = nullptr;            // [count][nslot][L] wide sigma mantissa (sigma >= 2^64)
+    int32_t* sX = nullptr;        // [count][nslot][L] wide sigma exponent, then psi exponent
+    uint8_t* wf = nullptr;        // [count][nslot][L] 1 where sigma >= 2^64
 };
 
-// Every batch of a weighted graph (weights in [1, W]); stats[0] += batches
-// done, stats[1] += settle steps, low word of stats[3] |= error bits (1: a
-// path count reached 2^64, 2: too many distinct distances, 4: queue full,
-// 8: a bucket list full).  k_dist/k_sigma (may be null) receive the
-// per-source state, rows by source position, n_total columns.
+// Every batch of a weighted graph (weights in [1, W]; wt null: all weights 1,
+// W = 1, an unweighted graph run pair by pair).  A batch whose path counts
+// pass 2^64 is rerun in the wide format and sets gwide[its graph]; batches
+// with .wide set, or of a graph with gwide set, start wide.  stats[0] +=
+// batches done, stats[1] += settle steps, stats[2] += batches rerun wide, low
+// word of stats[3] |= error bits (2: too many distinct distances, 4: queue
+// full, 8: a bucket list full).  k_dist/k_sigma/k_ovf (may be null) receive
+// the per-source state, rows by source position, n_total columns.
 cudaError_t launch_weighted_batches(const Csr& g, const int32_t* wt, const WSlots& S, const WBatch* batches, int nb,
                                     const int32_t* srcs, unsigned* next, u64* bc, int W, int32_t* k_dist,
-                                    u64* k_sigma, long long n_total, unsigned long long* stats, cudaStream_t st);
+                                    u64* k_sigma, uint8_t* k_ovf, long long n_total, int* gwide,
+                                    unsigned long long* stats, cudaStream_t st);
 
 // Clusters of csize CTAs of k_block_batches that fit on the device at once
 // (0 if the query fails).

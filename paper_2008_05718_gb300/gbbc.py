@@ -21,7 +21,7 @@ _lib = None
 
 GBBC_OK, GBBC_ERR_INVALID, GBBC_ERR_OOM, GBBC_ERR_CUDA, GBBC_ERR_TIMEOUT, GBBC_ERR_CAPACITY, GBBC_ERR_STATE = range(7)
 POLICY = {"auto": 0, "beamer": 1, "learned": 2, "push": 3, "pull": 4}
-SCHEDULE = {"auto": 0, "grid": 1, "block": 2}
+SCHEDULE = {"auto": 0, "grid": 1, "block": 2, "pair": 3}
 GBBC_KEEP_STATE = 1
 GBBC_TRACE = 2
 GBBC_TRACE_BOTH = 4

@@ -33,7 +33,7 @@ def check_w(gb, g, w, S, keep=(), **opts):
         d, s, o = st[i]
         assert np.array_equal(d, ost[i].dist), f"dist of source #{i}"
         assert np.array_equal(s, ost[i].sigma), f"sigma of source #{i}"
-        assert not o.any()
+        assert np.array_equal(o, ost[i].ovf), f"overflow flags of source #{i}"
     return got, fixed, stats
 
 
@@ -94,12 +94,20 @@ def test_weighted_edge_cases(gb):
     check_w(gb, h, wh, gg.sample_sources(h.n, 199, seed=215), keep=(64, 198))
 
 
-def test_weighted_overflow_and_invalid_weights(gb):
-    g = gg.diamond_chain(70)  # 2^70 shortest paths at unit weights
-    with gb.BC.from_weighted(g.n, g.row_ptr, g.col, np.ones(g.nnz, np.int32)) as bc:
-        with pytest.raises(gb.GbbcError) as e:
-            bc.compute([0])
-        assert e.value.status == gb.GBBC_ERR_CAPACITY
+def test_weighted_counts_past_2_64_run_wide(gb):
+    # 2^70 shortest paths at unit weights (diamond chain), C(2k, k) on grids:
+    # the batch is rerun in the wide format; sigma mod 2^64 and the flags
+    # stay exact, BC within tolerance
+    g = gg.diamond_chain(70)
+    S = np.arange(g.n, dtype=np.int32)
+    _, _, stats = check_w(gb, g, np.ones(g.nnz, np.int32), S, keep=(0, g.n - 1))
+    assert stats["wide_batches"] > 0
+    h = gg.grid(48, "0.05", seed=220)
+    wh = gg.edge_weights(h, 2, seed=221)
+    check_w(gb, h, wh, gg.sample_sources(h.n, 150, seed=222), keep=(0, 149))
+
+
+def test_weighted_invalid_weights(gb):
     h = gg.path(5)
     for bad in (np.zeros(h.nnz, np.int32), np.full(h.nnz, gb.MAX_WEIGHT + 1, np.int32)):
         with pytest.raises(gb.GbbcError) as e:
@@ -119,3 +127,42 @@ def test_weighted_full_size_sampled(gb):
     g, S = gg.workload("rmat18")
     w = gg.edge_weights(g, 16, seed=216)
     check_w(gb, g, w, S[:64], keep=(0, 63))
+
+
+# ---- the same kernel for unweighted graphs (GBBC_SCHEDULE_PAIR) ----------------
+
+PAIR_CASES = [
+    ("grid64_wide", lambda: gg.grid(64, "0.05", seed=230), 200),
+    ("tri48", lambda: gg.tri(48, seed=231), 160),
+    ("rgg3000", lambda: gg.rgg(3000, 10.0, seed=232), 300),
+    ("mesh12", lambda: gg.mesh27(12), 200),
+    ("rmat12", lambda: gg.rmat(12, 16, seed=233), 400),
+    ("diamond70", lambda: gg.diamond_chain(70), 211),
+]
+
+
+@pytest.mark.parametrize("name,make,k", PAIR_CASES, ids=[c[0] for c in PAIR_CASES])
+def test_pair_schedule_parity(gb, name, make, k):
+    import oracle as orc
+    g = make()
+    S = gg.sample_sources(g.n, min(k, g.n), seed=234)
+    keep = (0, len(S) - 1)
+    want, ost = orc.bc_graph(g, S, dump=keep)
+    with gb.BC.from_graph(g, schedule="pair", flags=gb.GBBC_KEEP_STATE) as bc:
+        bc.compute(S)
+        got = bc.read()
+        assert bc.stats()["schedule"] == 3
+        for i in keep:
+            d, s, o = bc.source_state(i)
+            assert np.array_equal(d, ost[i].dist)
+            assert np.array_equal(s, ost[i].sigma)
+            assert np.array_equal(o, ost[i].ovf)
+    assert_bc_close(got, want)
+    with gb.BC.from_graph(g, schedule="pair") as bc:
+        bc.compute(S)
+        pair_fixed = bc.read_fixed()
+        wide = bc.stats()["wide_batches"]
+    if wide == 0:  # counts below 2^64: the same integer sums as the bitset path
+        with gb.BC.from_graph(g, schedule="grid") as bc:
+            bc.compute(S)
+            assert np.array_equal(bc.read_fixed(), pair_fixed)
