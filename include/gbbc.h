@@ -91,10 +91,11 @@ typedef struct gbbc_options {
 
 /* How batches are mapped to the GPU. */
 enum gbbc_schedule {
-    GBBC_SCHEDULE_AUTO = 0,  /* one graph above 65,536 vertices with average
+    GBBC_SCHEDULE_AUTO = 0,  /* graphs above 65,536 vertices with average
                                 degree at most 12 and a BFS eccentricity of at
-                                least 64 (from a vertex of the largest row)
-                                runs pair; batches of other graphs above 65,536
+                                least 64 (from a vertex of the largest row) run
+                                pair when their sources in the call number at
+                                most 8 per SM; batches of other graphs above 65,536
                                 vertices with average degree above 6 run grid;
                                 for the rest, block when the batches fill the
                                 GPU, else the first call times some batches in

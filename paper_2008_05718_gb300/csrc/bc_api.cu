@@ -47,7 +47,7 @@ struct gbbc_graph {
     long long d_wb_cap = 0;
     std::vector<char> wide_graph;    // per graph: its batches start in the wide sigma format
     int max_clusters[4] = {0, 0, 0, 0};  // resident block-schedule clusters of 1, 2, 4, 8 CTAs
-    int pair_auto = -1;              // GBBC_SCHEDULE_AUTO takes the pair schedule: -1 not yet decided
+    std::vector<signed char> pair_graph;  // per graph: the auto schedule takes pair (1), not (0), undecided (-1)
     int* d_gwide = nullptr;          // per graph: set by the block schedule when a batch went wide
     Slot slot;
     bool slot_ready = false;
@@ -703,44 +703,52 @@ gbbc_status grouping_scores(gbbc_graph* g, const std::vector<int32_t>& src, cons
 // ids, `gid` their graph index.
 gbbc_status compute_weighted(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
                              cudaStream_t st);
+gbbc_status compute_batched(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
+                            cudaStream_t st, bool mixed);
 
-// Under GBBC_SCHEDULE_AUTO, one large sparse graph of high diameter runs in
-// the pair schedule: its sources rarely share a BFS level, so 64-lane rows
-// are mostly idle (measured: 1024^2 triangulation 1.54x, 2^20-point random
-// geometric graph 1.52x, 1024^2 grid 1.13x faster; the 100^3 mesh, degree 26,
-// and small or low-diameter graphs are faster in the bitset schedules).  The
-// test: one graph above 65,536 vertices, average degree at most 12, and a
-// BFS eccentricity of at least 64 from a vertex of the largest row (host BFS
-// over a host copy of the columns, once per handle).
-bool pair_auto(gbbc_graph* g) {
-    if (g->pair_auto >= 0) return g->pair_auto == 1;
-    g->pair_auto = 0;
-    const long long n = g->n;
-    if (g->goff.size() != 2 || n <= 65536 || (double)g->nnz > 12.0 * (double)n) return false;
-    std::vector<int32_t> col((size_t)g->nnz);
-    if (cudaMemcpy(col.data(), g->d_col, (size_t)g->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+// Under GBBC_SCHEDULE_AUTO, a large sparse graph of high diameter with few
+// sources runs in the pair schedule: its sources rarely share a BFS level, so
+// 64-lane rows are mostly idle (measured with 1024 sources: 1024^2
+// triangulation 1.54x, 2^20-point random geometric graph 1.52x, 1024^2 grid
+// 1.13x faster; the 100^3 mesh, degree 26, and small or low-diameter graphs
+// are faster in the bitset schedules).  The
+// test, per graph of the handle, once: above 65,536 vertices, average degree
+// at most 12, and a BFS eccentricity of at least 64 from a vertex of its
+// largest row (host BFS over a host copy of the columns).
+bool pair_auto(gbbc_graph* g, int gi) {
+    if (g->pair_graph.size() != g->goff.size() - 1) g->pair_graph.assign(g->goff.size() - 1, -1);
+    if (g->pair_graph[gi] >= 0) return g->pair_graph[gi] == 1;
+    g->pair_graph[gi] = 0;
+    const long long lo = g->goff[gi], hi = g->goff[gi + 1], n = hi - lo;
+    const long long e0 = g->h_row_ptr[lo], e1 = g->h_row_ptr[hi];
+    if (n <= 65536 || (double)(e1 - e0) > 12.0 * (double)n) return false;
+    std::vector<int32_t> col((size_t)(e1 - e0));
+    if (cudaMemcpy(col.data(), g->d_col + e0, (size_t)(e1 - e0) * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+        cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    int32_t s = 0;
-    for (int32_t v = 1; v < (int32_t)n; ++v)
+    long long s = lo;
+    for (long long v = lo + 1; v < hi; ++v)
         if (g->h_row_ptr[v + 1] - g->h_row_ptr[v] > g->h_row_ptr[s + 1] - g->h_row_ptr[s]) s = v;
     std::vector<int32_t> dist((size_t)n, -1), queue;
     queue.reserve((size_t)n);
-    dist[s] = 0;
-    queue.push_back(s);
+    dist[s - lo] = 0;
+    queue.push_back((int32_t)(s - lo));
     int32_t ecc = 0;
     for (size_t h = 0; h < queue.size(); ++h) {
         const int32_t v = queue[h];
-        for (int32_t p = g->h_row_ptr[v]; p < g->h_row_ptr[v + 1]; ++p)
-            if (dist[col[p]] < 0) {
-                dist[col[p]] = dist[v] + 1;
-                ecc = std::max(ecc, dist[v] + 1);
-                queue.push_back(col[p]);
+        for (int32_t p = g->h_row_ptr[lo + v]; p < g->h_row_ptr[lo + v + 1]; ++p) {
+            const int32_t u = col[p - e0] - (int32_t)lo;
+            if (dist[u] < 0) {
+                dist[u] = dist[v] + 1;
+                ecc = std::max(ecc, dist[u]);
+                queue.push_back(u);
             }
+        }
     }
-    g->pair_auto = ecc >= 64 ? 1 : 0;
-    return g->pair_auto == 1;
+    g->pair_graph[gi] = ecc >= 64 ? 1 : 0;
+    return g->pair_graph[gi] == 1;
 }
 
 gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
@@ -750,10 +758,38 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
         return fail(g, GBBC_ERR_STATE, "GBBC_POLICY_LEARNED needs weights (bc_policy_load)");
     CKS(alloc_keep(g, k, st));
     g->last_stream = st;
-    if (g->d_w || g->opt.schedule == GBBC_SCHEDULE_PAIR ||
-        (g->opt.schedule == GBBC_SCHEDULE_AUTO && g->opt.batch_width != 1 && !(g->opt.flags & GBBC_TRACE) &&
-         pair_auto(g)))
-        return compute_weighted(g, gsrc, gid, st);
+    if (g->d_w || g->opt.schedule == GBBC_SCHEDULE_PAIR) return compute_weighted(g, gsrc, gid, st);
+    if (g->opt.schedule == GBBC_SCHEDULE_AUTO && g->opt.batch_width != 1 && !(g->opt.flags & GBBC_TRACE)) {
+        const int ngraphs = (int)g->goff.size() - 1;
+        // the pair kernel gains by spreading few sources over every SM; with
+        // more than 8 sources per SM its batches are as wide as the bitset
+        // words and the words' shared rows win (256-graph mix: 13.2 s bitset,
+        // 19.4 s with its large grids in the pair kernel)
+        const long long pair_max = 8ll * g->nsm;
+        if (ngraphs == 1) {
+            if (k <= pair_max && pair_auto(g, 0)) return compute_weighted(g, gsrc, gid, st);
+        } else if (!g->k_dist) {  // kept state follows list order: no split then
+            // the sources of graphs the pair schedule takes go there, the rest below
+            std::vector<int32_t> ps, pg, rs, rg;
+            for (long long i = 0; i < k; ++i) {
+                const bool pr = pair_auto(g, gid[i]);
+                (pr ? ps : rs).push_back(gsrc[i]);
+                (pr ? pg : rg).push_back(gid[i]);
+            }
+            if (!ps.empty() && (long long)ps.size() <= pair_max) {
+                CKS(compute_weighted(g, ps, pg, st));
+                if (rs.empty()) return GBBC_OK;
+                return compute_batched(g, rs, rg, st, true);
+            }
+        }
+    }
+    return compute_batched(g, gsrc, gid, st, false);
+}
+
+// The bitset schedules (grid, block): sources packed 64 (or 32) per word.
+gbbc_status compute_batched(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
+                            cudaStream_t st, bool mixed) {
+    long long k = (long long)gsrc.size();
     if (g->opt.batch_width == 1) {  // plain: one source at a time, list order
         CKS(alloc_plain(g));
         for (long long i = 0; i < k; ++i)
@@ -797,7 +833,9 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
             return fail(g, GBBC_ERR_INVALID, "GBBC_KEEP_STATE needs the sources of each graph to be contiguous");
         batches.push_back(b);
     }
-    return dispatch(g, batches, st);
+    CKS(dispatch(g, batches, st));
+    if (mixed) g->stats.schedule = GBBC_SCHEDULE_AUTO;  // pair and bitset schedules in one call
+    return GBBC_OK;
 }
 
 // ---- weighted graphs ----------------------------------------------------------

@@ -447,7 +447,9 @@ def test_multi_workload_full_size_sampled(gb):
         for i in range(0, 256, 15):
             want, _ = oracle.bc_graph(mw.graphs[i], per[i])
             assert_bc_close(bc.read(graph_id=i), want)
-    assert st["batches"] == 256 and st["wide_batches"] > 0
+    # one bitset batch per graph, or one pair batch per source (L = 1 here) for
+    # the large grids the auto schedule sends to the pair kernel (144 sources)
+    assert st["batches"] >= 256 and st["wide_batches"] > 0
 
 
 def test_rmat22_full_size_sampled(gb):

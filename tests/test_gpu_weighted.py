@@ -166,3 +166,23 @@ def test_pair_schedule_parity(gb, name, make, k):
         with gb.BC.from_graph(g, schedule="grid") as bc:
             bc.compute(S)
             assert np.array_equal(bc.read_fixed(), pair_fixed)
+
+
+def test_auto_schedule_routes_high_diameter_graphs_of_a_multi_handle_to_pairs(gb):
+    # a large grid (above 65,536 vertices, eccentricity >= 64) goes to the pair
+    # schedule, the R-MAT graphs and the small grid to the bitset schedules;
+    # every graph's BC matches the oracle
+    import oracle as orc
+    graphs = [gg.rmat(10, 16, seed=240), gg.grid(300, "0.03", seed=241), gg.grid(40, "0.03", seed=242),
+              gg.rmat(11, 16, seed=243)]
+    per = [gg.sample_sources(g.n, min(100, g.n), seed=244 + i) for i, g in enumerate(graphs)]
+    gids = np.concatenate([np.full(len(S), i, np.int32) for i, S in enumerate(per)])
+    locs = np.concatenate(per).astype(np.int32)
+    with gb.BC.from_graphs(graphs) as bc:
+        bc.compute_multi(gids, locs)
+        st = bc.stats()
+        got = [bc.read(graph_id=i) for i in range(len(graphs))]
+    assert st["schedule"] == 0  # pair and bitset schedules in one call
+    for i, g in enumerate(graphs):
+        want, _ = orc.bc_graph(g, per[i])
+        assert_bc_close(got[i], want)
