@@ -343,6 +343,13 @@ def run_ours(args):
             "share_of_step": p["ms"] / total_ms if total_ms else None, "peak_source": f"{peak_src} hbm_gbs (copy)",
             "steps": {x: {"ms": round(v["ms"], 3), "GBps": (v["bytes"] / v["ms"] / 1e6) if v["ms"] else 0.0}
                       for x, v in prof.items()}}
+    # the whole step in the timed region: every step kind's algorithmic bytes
+    # (from the traced step, whose batches run one at a time) over the timed
+    # step time (batches overlap there, on several streams)
+    step_bytes = sum(v["bytes"] for v in prof.values())
+    roof["timed_step"] = {"algorithmic_bytes": step_bytes, "ms": 1e3 * total_s / args.steps,
+                          "GBps": step_bytes / total_s * args.steps / 1e9,
+                          "frac": step_bytes / total_s * args.steps / 1e9 / peak}
 
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None

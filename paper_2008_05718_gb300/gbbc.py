@@ -41,7 +41,7 @@ class gbbc_options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("batch_width", ctypes.c_int32), ("policy", ctypes.c_int32),
                 ("validate", ctypes.c_int32), ("timeout_spins", ctypes.c_int64), ("flags", ctypes.c_uint32),
                 ("heavy_degree", ctypes.c_int32), ("mem_limit_bytes", ctypes.c_int64),
-                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("streams", ctypes.c_int32)]
 
 
 class gbbc_stats(ctypes.Structure):
@@ -182,7 +182,7 @@ def _as_i32(buf):
 
 
 def options(batch_width=0, policy="auto", validate=False, flags=0, heavy_degree=0, mem_limit_bytes=0,
-            timeout_spins=0, schedule="auto") -> gbbc_options:
+            timeout_spins=0, schedule="auto", streams=0) -> gbbc_options:
     o = gbbc_options()
     load().bc_options_init(ctypes.byref(o))
     o.batch_width = int(batch_width)
@@ -193,6 +193,7 @@ def options(batch_width=0, policy="auto", validate=False, flags=0, heavy_degree=
     o.mem_limit_bytes = int(mem_limit_bytes)
     o.timeout_spins = int(timeout_spins)
     o.schedule = SCHEDULE[schedule] if isinstance(schedule, str) else int(schedule)
+    o.streams = int(streams)
     return o
 
 

@@ -373,6 +373,28 @@ def test_planar_geometric_and_mesh_full_size_sampled(gb, name, nsrc):
     check(gb, g, S[:nsrc], keep=(0, nsrc - 1))
 
 
+@pytest.mark.parametrize("make,k", [(lambda: gg.rmat(12, 16, seed=250), 1000), (lambda: gg.grid(64, "0.05", seed=251), 400),
+                                    (lambda: gg.diamond_chain(70), 211)])
+def test_concurrent_grid_batches_give_identical_bits(gb, make, k):
+    # the grid schedule with 1, 2 and 4 batches at once (own streams, slots and
+    # BC accumulators, summed exactly): the same bits, and the oracle's BC
+    g = make()
+    S = gg.sample_sources(g.n, min(k, g.n), seed=252)
+    ref = None
+    for streams in (1, 2, 4):
+        with gb.BC.from_graph(g, schedule="grid", streams=streams) as bc:
+            bc.compute(S)
+            fixed = bc.read_fixed()
+            got = bc.read()
+            st = bc.stats()
+        assert st["batches"] == (len(S) + 63) // 64
+        if ref is None:
+            ref = fixed
+            want, _ = oracle.bc_graph(g, S)
+            assert_bc_close(got, want)
+        assert np.array_equal(fixed, ref)
+
+
 def test_block_schedule_multi_graph_and_width32(gb):
     graphs = [gg.rmat(10, 16, seed=71), gg.grid(40, "0.03", seed=72), gg.path(50), gg.rmat(11, 16, seed=73)]
     gids, locs, per = [], [], []
