@@ -88,9 +88,9 @@ typedef struct gbbc_options {
     int32_t schedule;      /* enum gbbc_schedule */
     int32_t streams;       /* batches the grid schedule runs at once, each on
                               its own stream and slot (BC summed exactly at
-                              the end of the call): 0 = auto (4, fewer when
-                              memory is short), 1 = one at a time; tracing
-                              and kept state run one at a time */
+                              the end of the call): 0 = auto (8, fewer when
+                              memory is short), 1 = one at a time, at most
+                              16; tracing and kept state run one at a time */
 } gbbc_options;
 
 /* How batches are mapped to the GPU. */

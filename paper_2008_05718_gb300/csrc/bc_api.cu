@@ -1251,17 +1251,17 @@ void stats_add(gbbc_stats& a, gbbc_stats& b) {
     std::memset(&b, 0, sizeof(b));
 }
 
-// Concurrent batches of the grid schedule: up to opt.streams (default 4)
+// Concurrent batches of the grid schedule: up to opt.streams (default 8)
 // batches at once, worker 0 on the caller's stream and slot, the others on
 // their own streams, slots and fixed-point BC accumulators, each driven by a
 // host thread taking the next batch from a shared counter.  A single batch's
 // levels leave much of the GPU idle (small frontiers, host read-back per
 // level); overlapping batches fills it (R-MAT 18, 4096 sources: 1.36x with 2,
-// 1.56x with 4).  The accumulators are added into the handle's BC at the end:
+// 1.56x with 4, 1.63x with 6, 1.66x with 8).  The accumulators are added into the handle's BC at the end:
 // integer sums, so BC does not depend on which worker ran which batch.
 int grid_workers(gbbc_graph* g, size_t nb) {
     if ((g->opt.flags & GBBC_TRACE) || g->k_dist || nb < 2) return 1;
-    int want = g->opt.streams == 0 ? 4 : g->opt.streams;
+    int want = g->opt.streams == 0 ? 8 : g->opt.streams;
     want = (int)std::min<size_t>((size_t)want, nb);
     if (want <= 1) return 1;
     const double n = (double)std::max<int32_t>(g->n, 1);
