@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--workload", default="rmat18", choices=sorted(WORKLOADS))
     ap.add_argument("--policy", default="auto")
     ap.add_argument("--width", type=int, default=64)
+    ap.add_argument("--schedule", default="auto", choices=["auto", "grid", "block", "pair"])
     ap.add_argument("--streams", type=int, default=0,
                     help="batches the grid schedule runs at once (0: the library's default)")
     ap.add_argument("--grouping", default="learned", choices=["learned", "none"],
@@ -243,7 +244,7 @@ def run_ours(args):
     src = torch.from_numpy(S).to(dev)
     out = torch.zeros(g.n, dtype=torch.float64, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    opts = dict(batch_width=args.width, policy=args.policy, streams=args.streams)
+    opts = dict(batch_width=args.width, policy=args.policy, streams=args.streams, schedule=args.schedule)
 
     weights = None
     if args.policy in ("auto", "learned") and args.width != 1:
