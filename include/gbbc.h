@@ -350,6 +350,14 @@ gbbc_status bc_graph_create_weighted(int32_t n, int64_t nnz, const int32_t* row_
                                      gbbc_graph** out);
 
 /*
+ * bc_release_memory - the library takes device memory from one pool per
+ * device and keeps what destroyed handles free (so the next handle's
+ * allocations are immediate).  This returns the unused part of device's pool
+ * (-1: the current device) to the driver.  Synchronises the device.
+ */
+gbbc_status bc_release_memory(int32_t device);
+
+/*
  * Learned source grouping.  A network of the same shape with K = 1 output
  * scores each source from six features (bc_source_features: log-scaled
  * degree of s, sum and maximum of its neighbours' degrees, and the size,

@@ -35,6 +35,7 @@ cudaError_t policy_to_half(const float* params_dev, void* half_dev, cudaStream_t
 
 struct gbbc_graph {
     int device = 0;
+    cudaStream_t ast = nullptr;      // stream of the library's pool allocations and frees
     int nsm = 152;
     int32_t n = 0;
     long long nnz = 0;
@@ -141,6 +142,53 @@ void release_failed(gbbc_graph* g, gbbc_status r) {
         if (s_ != GBBC_OK) return s_;      \
     } while (0)
 
+// Device memory comes from one stream-ordered pool per device, shared by the
+// library's handles and never shrunk by itself (release threshold: all), so a
+// handle created after another was destroyed finds its slots' memory ready;
+// bc_release_memory gives the unused part back.  A pool allocation is made on
+// the handle's allocation stream and synchronised, so every stream may use it;
+// a free first synchronises the device (as cudaFree does).
+std::mutex g_pool_mtx;
+cudaMemPool_t g_pools[64] = {};
+
+cudaMemPool_t device_pool(int dev) {
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mtx);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+
+// Free device memory plus what the library's pool holds unused.
+size_t avail_bytes(int dev) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaMemPool_t pool = device_pool(dev);
+    if (pool) {
+        uint64_t reserved = 0, used = 0;
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+        if (reserved > used) free_b += (size_t)(reserved - used);
+    }
+    return free_b;
+}
+
 gbbc_status dalloc(gbbc_graph* g, void** p, size_t bytes) {
     std::lock_guard<std::recursive_mutex> lk(g->mtx);
     *p = nullptr;
@@ -148,7 +196,14 @@ gbbc_status dalloc(gbbc_graph* g, void** p, size_t bytes) {
     if (g->opt.mem_limit_bytes > 0 && g->bytes + bytes > (size_t)g->opt.mem_limit_bytes)
         return fail(g, GBBC_ERR_OOM, "allocation of %zu bytes exceeds mem_limit_bytes=%lld (held %zu)", bytes,
                     (long long)g->opt.mem_limit_bytes, g->bytes);
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaMemPool_t pool = g->ast ? device_pool(g->device) : nullptr;
+    cudaError_t e;
+    if (pool) {
+        e = cudaMallocFromPoolAsync(p, bytes, pool, g->ast);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->ast);
+    } else {
+        e = cudaMalloc(p, bytes);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -173,7 +228,12 @@ void dfree(gbbc_graph* g, void* p) {
             g->allocs.erase(g->allocs.begin() + i);
             break;
         }
-    cudaFree(p);
+    if (g->ast && device_pool(g->device)) {
+        cudaDeviceSynchronize();
+        cudaFreeAsync(p, g->ast);
+    } else {
+        cudaFree(p);
+    }
 }
 
 bool is_device_ptr(const void* p) {
@@ -248,6 +308,7 @@ gbbc_status read_options(gbbc_graph* g, const gbbc_options* opt) {
 gbbc_status init_device(gbbc_graph* g) {
     CK(g, cudaGetDevice(&g->device));
     CK(g, cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, g->device));
+    CK(g, cudaStreamCreateWithFlags(&g->ast, cudaStreamNonBlocking));
     return GBBC_OK;
 }
 
@@ -895,9 +956,7 @@ gbbc_status alloc_wslots(gbbc_graph* g, long long nslot, int L, int B, int want)
     const long long levcap = 2 * nslot + 4096;
     const long long bcap = nslot * L;  // a pair is listed at most once per bucket between its visits
     const double per_slot = wslot_bytes(nslot, L, B);
-    size_t free_b = 0, total_b = 0;
-    CK(g, cudaMemGetInfo(&free_b, &total_b));
-    double budget = 0.5 * (double)free_b;
+    double budget = 0.5 * (double)avail_bytes(g->device);
     if (g->opt.mem_limit_bytes > 0) budget = std::min(budget, (double)g->opt.mem_limit_bytes - (double)g->bytes);
     int count = (int)std::min<double>((double)want, std::floor(budget / per_slot));
     if (count < 1) return fail(g, GBBC_ERR_OOM, "no room for one weighted-path slot (%.0f bytes)", per_slot);
@@ -1025,9 +1084,7 @@ gbbc_status alloc_block(gbbc_graph* g, long long nslot, int want) {
     const long long qcap = nslot * kLanes + kLanes;
     const double per_slot = (double)nslot * (3 * 8 + 2 * sizeof(MaskTag) + kLanes * (8 + 8 + 8 + 4 + 4) + 8) +
                             (double)qcap * 12 + sizeof(Counters);
-    size_t free_b = 0, total_b = 0;
-    CK(g, cudaMemGetInfo(&free_b, &total_b));
-    double budget = 0.5 * (double)free_b;
+    double budget = 0.5 * (double)avail_bytes(g->device);
     if (g->opt.mem_limit_bytes > 0) budget = std::min(budget, (double)g->opt.mem_limit_bytes - (double)g->bytes);
     int count = (int)std::min<double>((double)want, std::floor(budget / per_slot));
     if (count < 1) return fail(g, GBBC_ERR_OOM, "no room for one block-schedule slot (%.0f bytes)", per_slot);
@@ -1267,12 +1324,7 @@ int grid_workers(gbbc_graph* g, size_t nb) {
     const double n = (double)std::max<int32_t>(g->n, 1);
     // per extra worker: the slot (as alloc_slot_into) and its BC accumulator
     const double per = n * (3 * 8 + 2 * sizeof(MaskTag) + kLanes * 16 + 8 + 8) + (n * kLanes + kLanes) * 12 + 16 * n;
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-        cudaGetLastError();
-        return 1;
-    }
-    double budget = 0.5 * (double)free_b;
+    double budget = 0.5 * (double)avail_bytes(g->device);
     if (g->opt.mem_limit_bytes > 0) budget = std::min(budget, (double)g->opt.mem_limit_bytes - (double)g->bytes);
     const int have = (int)g->workers.size();
     const int fit = have + (int)std::max(0.0, std::floor(budget / per));
@@ -1743,8 +1795,16 @@ gbbc_status bc_sync(gbbc_graph* g) {
 void bc_graph_destroy(gbbc_graph* g) {
     if (!g) return;
     cudaDeviceSynchronize();
-    for (auto& a : g->allocs) cudaFree(a.first);
+    const bool pooled = g->ast && device_pool(g->device);
+    for (auto& a : g->allocs) {
+        if (pooled) cudaFreeAsync(a.first, g->ast);
+        else cudaFree(a.first);
+    }
     g->allocs.clear();
+    if (g->ast) {
+        cudaStreamSynchronize(g->ast);
+        cudaStreamDestroy(g->ast);
+    }
     if (g->slot.hctr) cudaFreeHost(g->slot.hctr);
     for (auto& w : g->workers) {
         if (w.slot.hctr) cudaFreeHost(w.slot.hctr);
@@ -1793,6 +1853,21 @@ gbbc_status bc_policy_load(gbbc_graph* g, const float* params, size_t bytes) {
     if (r == GBBC_OK && cudaStreamSynchronize(g->last_stream) != cudaSuccess) r = fail(g, GBBC_ERR_CUDA, "sync");
     dfree(g, tmp);
     return r;
+}
+
+gbbc_status bc_release_memory(int32_t device) {
+    int dev = device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return GBBC_ERR_CUDA;
+    }
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool) return GBBC_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemPoolTrimTo(pool, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return GBBC_ERR_CUDA;
+    }
+    return GBBC_OK;
 }
 
 gbbc_status bc_grouping_load(gbbc_graph* g, const float* params, size_t bytes) {

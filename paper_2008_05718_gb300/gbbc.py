@@ -32,7 +32,7 @@ EXPORTS = ("bc_options_init", "bc_graph_create", "bc_graph_create_multi", "bc_gr
            "bc_last_error_detail", "bc_get_stats", "bc_get_trace", "bc_clear_trace", "bc_get_profile",
            "bc_compute_noalloc", "bc_mlp_param_count", "bc_mlp_forward", "bc_mlp_loss_grad", "bc_mlp_adam_step",
            "bc_mlp_train", "bc_policy_eval", "bc_policy_load", "bc_read_fixed", "bc_source_features",
-           "bc_grouping_load", "bc_grouping_scores")
+           "bc_grouping_load", "bc_grouping_scores", "bc_release_memory")
 NOALLOC_MAX_VERTICES = 16384
 MAX_WEIGHT = 64  # GBBC_MAX_WEIGHT
 
@@ -119,6 +119,7 @@ def load():
             "bc_policy_eval": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
             "bc_policy_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
             "bc_grouping_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+            "bc_release_memory": (ctypes.c_int, [i32]),
             "bc_source_features": (ctypes.c_int, [vp, vp, i64, vp, vp]),
             "bc_grouping_scores": (ctypes.c_int, [vp, vp, i64, vp, vp]),
         }
@@ -436,6 +437,11 @@ def bc_grouping_scores(handle, sources, stream=None):
     out = np.zeros(len(src), np.float32)
     _check(load().bc_grouping_scores(handle, src.ctypes.data, len(src), out.ctypes.data, _stream(stream)), handle)
     return out
+
+
+def bc_release_memory(device=-1):
+    """Return the library pool's unused device memory to the driver."""
+    _check(load().bc_release_memory(int(device)))
 
 
 def bc_grouping_load(handle, params):
