@@ -395,6 +395,22 @@ def test_concurrent_grid_batches_give_identical_bits(gb, make, k):
         assert np.array_equal(fixed, ref)
 
 
+def test_released_pool_memory_is_taken_again(gb):
+    # handles draw on the library's pool; releasing its unused part between
+    # handles changes nothing in the results
+    g = gg.rmat(11, 16, seed=260)
+    S = gg.sample_sources(g.n, 300, seed=261)
+    outs = []
+    for release in (False, True, False):
+        if release:
+            gb.bc_release_memory()
+        with gb.BC.from_graph(g) as bc:
+            bc.compute(S)
+            outs.append(bc.read_fixed())
+    gb.bc_release_memory(-1)
+    assert all(np.array_equal(o, outs[0]) for o in outs)
+
+
 def test_block_schedule_multi_graph_and_width32(gb):
     graphs = [gg.rmat(10, 16, seed=71), gg.grid(40, "0.03", seed=72), gg.path(50), gg.rmat(11, 16, seed=73)]
     gids, locs, per = [], [], []
