@@ -52,6 +52,7 @@ struct gbbc_graph {
     long long d_wb_cap = 0;
     std::vector<char> wide_graph;    // per graph: its batches start in the wide sigma format
     int max_clusters[4] = {0, 0, 0, 0};  // resident block-schedule clusters of 1, 2, 4, 8 CTAs
+    int w_bps = 0;                   // resident pair-kernel blocks per SM (0: not yet asked)
     std::vector<signed char> pair_graph;  // per graph: the auto schedule takes pair (1), not (0), undecided (-1)
     int* d_gwide = nullptr;          // per graph: set by the block schedule when a batch went wide
     Slot slot;
@@ -864,7 +865,10 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
         // more than 8 sources per SM its batches are as wide as the bitset
         // words and the words' shared rows win (256-graph mix: 13.2 s bitset,
         // 19.4 s with its large grids in the pair kernel)
-        const long long pair_max = 8ll * g->nsm;
+#ifndef GBBC_PAIR_MAX_PER_SM
+#define GBBC_PAIR_MAX_PER_SM 8
+#endif
+        const long long pair_max = (long long)GBBC_PAIR_MAX_PER_SM * g->nsm;
         if (ngraphs == 1) {
             if (k <= pair_max && pair_auto(g, 0)) return compute_weighted(g, gsrc, gid, st);
         } else if (!g->k_dist) {  // kept state follows list order: no split then
@@ -999,8 +1003,11 @@ gbbc_status compute_weighted(gbbc_graph* g, const std::vector<int32_t>& gsrc, co
     for (long long i = 0; i < k; ++i)
         nslot = std::max<long long>(nslot, g->goff[gid[i] + 1] - g->goff[gid[i]]);
     // a slot's memory grows with L, so when fewer slots than SMs fit, wider
-    // batches do not raise the number of pairs in flight: L depends on k only
-    const int L = (int)std::max<long long>(1, std::min<long long>(kLanes, (k + g->nsm - 1) / g->nsm));
+    // batches do not raise the number of pairs in flight: L depends on k and
+    // on the resident blocks only (every resident block gets a batch)
+    if (g->w_bps == 0) g->w_bps = weighted_blocks_per_sm();
+    const long long blocks = (long long)g->nsm * g->w_bps;
+    const int L = (int)std::max<long long>(1, std::min<long long>(kLanes, (k + blocks - 1) / blocks));
     if ((double)nslot * L >= 2147483647.0)
         return fail(g, GBBC_ERR_INVALID, "weighted path: n x lanes must stay below 2^31");
     std::vector<WBatch> hb;
@@ -1026,7 +1033,7 @@ gbbc_status compute_weighted(gbbc_graph* g, const std::vector<int32_t>& gsrc, co
         hb.push_back(b);
     }
     const int nb = (int)hb.size();
-    CKS(alloc_wslots(g, nslot, L, W + 1, std::min(nb, g->nsm)));
+    CKS(alloc_wslots(g, nslot, L, W + 1, (int)std::min<long long>(nb, blocks)));
     const size_t ngraphs = g->wide_graph.size();
     if (!g->d_gwide) CKS(dalloc_t(g, &g->d_gwide, ngraphs));
     CK(g, cudaMemsetAsync(g->d_gwide, 0, ngraphs * sizeof(int), st));

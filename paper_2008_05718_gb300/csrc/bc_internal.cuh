@@ -169,10 +169,16 @@ void launch_undo(const Slot& s, long long q_lo, long long q_hi, cudaStream_t st)
 // Block-per-batch persistent kernel over `nb` batches; stats[0..3]: batches,
 // forward levels, bottom-up levels, wide reruns (device, accumulated).
 // ---- weighted graphs (bc_weighted.cu) ----
-constexpr int kWThreads = 512;   // one CTA per batch
+#ifndef GBBC_WTHREADS
+#define GBBC_WTHREADS 512
+#endif
+constexpr int kWThreads = GBBC_WTHREADS;  // one CTA per batch
 constexpr int kMaxWeight = 64;   // weights in [1, kMaxWeight]
 constexpr int kMaxBuckets = kMaxWeight + 1;
-constexpr int kWHeavy = 64;      // rows longer than this are scanned by a whole warp
+#ifndef GBBC_WHEAVY
+#define GBBC_WHEAVY 64
+#endif
+constexpr int kWHeavy = GBBC_WHEAVY;  // rows longer than this are scanned by a whole warp
 
 struct WBatch {
     int32_t lo, hi, nsrc, gi;
@@ -197,6 +203,8 @@ struct WSlots {
     uint8_t* wf = nullptr;        // [count][nslot][L] 1 where sigma >= 2^64
 };
 
+// Resident blocks of the pair-granular kernel per SM.
+int weighted_blocks_per_sm();
 // Every batch of a weighted graph (weights in [1, W]; wt null: all weights 1,
 // W = 1, an unweighted graph run pair by pair).  A batch whose path counts
 // pass 2^64 is rerun in the wide format and sets gwide[its graph]; batches

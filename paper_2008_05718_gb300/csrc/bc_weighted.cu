@@ -494,6 +494,15 @@ __global__ void __launch_bounds__(kWThreads) k_weighted_batches(Csr g, const int
     }
 }
 
+int weighted_blocks_per_sm() {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_weighted_batches, kWThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return b < 1 ? 1 : b;
+}
+
 cudaError_t launch_weighted_batches(const Csr& g, const int32_t* wt, const WSlots& S, const WBatch* batches, int nb,
                                     const int32_t* srcs, unsigned* next, u64* bc, int W, int32_t* k_dist,
                                     u64* k_sigma, uint8_t* k_ovf, long long n_total, int* gwide,
