@@ -112,8 +112,9 @@ enum gbbc_schedule {
                                 launch per call; the level loop runs on the
                                 device (cluster barriers only) */
     GBBC_SCHEDULE_PAIR = 3   /* the weighted graphs' kernel with all weights
-                                1: one block per batch of ceil(k / SMs)
-                                sources, work items (vertex, source) pairs,
+                                1: one block per batch of ceil(k / resident
+                                blocks) sources (at most 64), work items
+                                (vertex, source) pairs,
                                 for graphs whose sources rarely share a BFS
                                 level (high diameter); one launch per call.
                                 BC agrees with the other schedules to

@@ -987,8 +987,10 @@ gbbc_status alloc_wslots(gbbc_graph* g, long long nslot, int L, int B, int want)
 // Pair-granular kernel (bc_weighted.cu), for weighted graphs and for
 // unweighted ones under GBBC_SCHEDULE_PAIR (all weights 1): sources in list
 // order (by graph), L per batch, one CTA per batch, every batch in one
-// launch.  L = ceil(k / nsm), at most 64, so that the batches cover the SMs:
-// work items are (vertex, lane) pairs, so narrower batches lose nothing.
+// launch.  L = ceil(k / (SMs x resident blocks per SM)), at most 64, so that
+// every resident block gets a batch (one block per SM left it latency-bound;
+// two gave 1.5-1.6x).  Work items are (vertex, lane) pairs, so narrower
+// batches lose nothing.
 gbbc_status compute_weighted(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
                              cudaStream_t st) {
     if (g->opt.batch_width == 1)

@@ -3,7 +3,7 @@
 // phase, Sec. IV-C, which names BFS and SSSP side by side), and the same
 // kernel with all weights 1 for unweighted graphs whose sources rarely share
 // a level (high-diameter graphs).  A batch holds L sources (lanes) and one
-// CTA runs one batch; the host picks L so that the batches cover every SM.
+// CTA runs one batch; the host picks L so that every resident CTA gets one.
 // Work items are (vertex, lane) pairs: when the lanes of a vertex rarely
 // share a distance, rows of all lanes would be mostly idle.
 //
