@@ -47,6 +47,8 @@ WORKLOADS = {
     "rgg20": "random geometric graph, 2^20 uniform points, expected degree 10, LCC, seed 7, 1024 uniform sources",
     "mesh100": "100x100x100 mesh, 27-point stencil (KKT-like banded pattern, average degree 25.5), "
                "4096 uniform sources (seed 8)",
+    "grid256": "256x256 4-neighbour grid, 5% edges removed, LCC, seed 3256, 256 uniform sources "
+               "(a small case for profiling)",
     "wrmat18": "the rmat18 graph and sources with integer edge weights uniform in [1, 16] (seed 216); "
                "weighted shortest paths",
     "wgrid1024": "the grid1024 graph and sources with integer edge weights uniform in [1, 16] (seed 217); "
