@@ -277,24 +277,25 @@ __device__ bool w_batch(const Csr& g, const WView& v, const WBatch& bb, const in
     }
     __syncthreads();
     // ---- forward: settle distances D = 0, 1, ... in bucket order ----
+    // Two block barriers per distance: after the settle, and after the relax.
+    // Every thread finds the next non-empty bucket itself (the counts do not
+    // change between the relax barrier and the next settle), and the queue
+    // does not grow during the relax, so the step's first entry is the
+    // previous step's end.
     long long D = 0;
+    unsigned long long qprev = 0ull;
     for (;;) {
-        if (tid == 0) {
-            int found = -1;
-            for (int i = 0; i < B; ++i)
-                if (v.cnt[(int)((D + i) % B)] > 0) {
-                    found = i;
-                    break;
-                }
-            *v.done = found < 0;
-            *v.Dsh = D + (found < 0 ? 0 : found);
-        }
-        __syncthreads();
-        if (*v.done) break;
-        D = *v.Dsh;
+        int found = -1;
+        for (int i = 0; i < B; ++i)
+            if (v.cnt[(int)((D + i) % B)] > 0) {
+                found = i;
+                break;
+            }
+        if (found < 0 || *v.err) break;
+        D += found;
         const int bi = (int)(D % B);
         const int cnt = min(v.cnt[bi], (int)v.bcap);
-        const unsigned long long q0 = *v.tail;
+        const unsigned long long q0 = qprev;
         // settle; sigma of pairs with short rows
         for (int i = tid; i < cnt; i += blockDim.x) {
             const uint32_t pr = v.blist[(long long)bi * v.bcap + i];
@@ -343,19 +344,19 @@ __device__ bool w_batch(const Csr& g, const WView& v, const WBatch& bb, const in
                 if (WIDE) s = warp_wsum(s);
                 if (lane == 0) store_sigma<WIDE>(v, pr, a, s);
             }
-        if (tid == 0) {
+        if (tid == 0) {  // bucket bi is consumed; the relax never adds to it
             v.cnt[bi] = 0;
             if (*v.steps < v.levcap) {
                 v.levD[*v.steps] = (int32_t)D;
                 v.levOff[*v.steps] = (long long)q0;
                 ++*v.steps;
             } else {
-                *v.err |= 2u;
+                atomicOr(v.err, 2u);
             }
         }
-        __syncthreads();
-        if (*v.err) break;
-        // relax: short rows by a thread, long rows by a warp
+        // relax (alongside the long rows' sigma above, which reads only
+        // settled pairs, while the relax lowers only distances above D):
+        // short rows by a thread, long rows by a warp
         for (long long e = (long long)q0 + tid; e < (long long)q1; e += blockDim.x) {
             const uint32_t pr = v.qv[e];
             const int32_t w = (int32_t)(pr / L), j = (int32_t)(pr % L);
@@ -371,6 +372,7 @@ __device__ bool w_batch(const Csr& g, const WView& v, const WBatch& bb, const in
             for (int32_t p = beg + lane; p < end; p += 32) relax_edge(v, D, __ldg(g.col + p) - lo, j, wgt(v, p));
         }
         __syncthreads();
+        qprev = q1;
         D += 1;
     }
     if (tid == 0) v.levOff[*v.steps] = (long long)min((unsigned long long)v.qcap, *v.tail);
