@@ -162,8 +162,6 @@ struct WView {
     unsigned* err;
     unsigned long long* tail;
     int* steps;
-    int* done;
-    long long* Dsh;
     long long bcap, qcap, levcap;
     int L, B;
 };
@@ -447,8 +445,7 @@ __global__ void __launch_bounds__(kWThreads) k_weighted_batches(Csr g, const int
                                                                 u64* k_sigma, uint8_t* k_ovf, long long n_total,
                                                                 int* gwide, unsigned long long* stats) {
     __shared__ int s_cnt[kMaxBuckets];
-    __shared__ int s_b, s_done, s_steps;
-    __shared__ long long s_D;
+    __shared__ int s_b, s_steps;
     __shared__ unsigned s_err;
     __shared__ unsigned long long s_tail;
     const int tid = threadIdx.x;
@@ -469,8 +466,6 @@ __global__ void __launch_bounds__(kWThreads) k_weighted_batches(Csr g, const int
     v.err = &s_err;
     v.tail = &s_tail;
     v.steps = &s_steps;
-    v.done = &s_done;
-    v.Dsh = &s_D;
     v.bcap = S.bcap;
     v.qcap = S.qcap;
     v.levcap = S.levcap;
