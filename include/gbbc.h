@@ -1,6 +1,7 @@
 /*
  * gbbc.h - C ABI of libgbbc.so: exact Brandes betweenness centrality on one
- * GB300 (sm_103a), unweighted undirected graphs, the whole graph in HBM.
+ * GB300 (sm_103a), undirected graphs (unweighted, or with integer edge
+ * weights: bc_graph_create_weighted), the whole graph in HBM.
  *
  * The problem statement follows Sec. II of the paper: the input is a graph
  * with N vertices and M edges and a set of sources (Algorithm 1's input);
@@ -15,11 +16,13 @@
  *    current device; the library tells them apart with
  *    cudaPointerGetAttributes.  The caller owns all buffers it passes in;
  *    the library copies inputs before returning and owns all device memory
- *    it allocates (released by bc_graph_destroy).
+ *    it allocates (released by bc_graph_destroy into the library's pool,
+ *    which bc_release_memory empties).
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
- *    enqueued on it; a call may synchronize it internally.  One handle must
- *    not be used from two host threads at once, and calls on one handle are
- *    ordered on the stream given to them.
+ *    enqueued on it; a call may synchronize it internally, and may run
+ *    batches on streams of its own (joined back to `stream` before it
+ *    returns).  One handle must not be used from two host threads at once,
+ *    and calls on one handle are ordered on the stream given to them.
  *  - Device-side failures (queue capacity, sigma width, a bounded device
  *    wait that gave up) are detected by the library and reported as status
  *    codes; no kernel traps.
