@@ -1412,7 +1412,10 @@ double now_s() {
 // kBlockMaxAvgDegree run in the grid schedule: one cluster per batch cannot
 // hide the latency of their wide levels.  Sparse large graphs (road-like,
 // thousands of levels) run block: their cost is per level, not per edge.
-constexpr long long kBlockMaxVertices = 65536;
+#ifndef GBBC_BLOCK_MAX_VERTICES
+#define GBBC_BLOCK_MAX_VERTICES 65536
+#endif
+constexpr long long kBlockMaxVertices = GBBC_BLOCK_MAX_VERTICES;
 constexpr double kBlockMaxAvgDegree = 6.0;
 
 bool grid_graph(const gbbc_graph* g, const BatchDesc& b) {
