@@ -90,3 +90,36 @@ def test_product_path_has_no_oracle_dependency():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text, f
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    # a C99 program includes the header, links libgbbc.so and calls the
+    # entry points that need no GPU
+    from paper_2008_05718_gb300 import _build
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "gbbc.h"
+int main(void) {
+    gbbc_options o;
+    bc_options_init(&o);
+    if (o.struct_size != sizeof(gbbc_options) || o.schedule != GBBC_SCHEDULE_AUTO || o.streams != 0) return 1;
+    if (strcmp(bc_status_string(GBBC_ERR_CAPACITY), "GBBC_ERR_CAPACITY") != 0) return 2;
+    if (bc_mlp_param_count(2) <= 0 || bc_mlp_param_count(1) >= bc_mlp_param_count(2)) return 3;
+    gbbc_graph* g = (gbbc_graph*)0;
+    int32_t rp[2] = {0, 0};
+    if (bc_graph_create(-1, 0, rp, (const int32_t*)0, &o, (void*)0, &g) != GBBC_ERR_INVALID || g) return 4;
+    if (bc_compute((gbbc_graph*)0, (const int32_t*)0, 0, (void*)0) != GBBC_ERR_INVALID) return 5;
+    printf("ok %d %d\n", GBBC_MAX_WEIGHT, GBBC_NOALLOC_MAX_VERTICES);
+    return 0;
+}
+''')
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(_build.LIB)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-L", libdir, "-l:" + os.path.basename(_build.LIB), "-Wl,-rpath," + libdir,
+                           "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, (out.returncode, out.stderr[-500:])
+    assert out.stdout.split() == ["ok", "64", "16384"]
