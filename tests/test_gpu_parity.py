@@ -87,6 +87,41 @@ def test_rmat18_full_size_sampled(gb):
     check(gb, g, S[:64], keep=(0, 31, 63), batch_width=64, policy="auto")
 
 
+def _bench_handle(gb, g, **opts):
+    from paper_2008_05718_gb300 import grouping, policy
+    bc = gb.BC.from_graph(g, **opts)
+    bc.load_policy(policy.shipped_weights())
+    bc.load_grouping(grouping.shipped_weights())
+    return bc
+
+
+@pytest.mark.parametrize("name,k", [("rmat18", None), ("rmat22", 512)])
+def test_bench_configuration_gives_the_bits_of_one_batch_at_a_time(gb, name, k):
+    # the benchmark's launch configuration (learned direction and grouping, 8
+    # batches at once on their own streams) at full size against one batch at
+    # a time in list order under the threshold rule: the same integer BC
+    g, S = gg.workload(name)
+    S = S if k is None else S[:k]
+    with _bench_handle(gb, g) as bc:
+        bc.compute(S)
+        fast = bc.read_fixed()
+        st = bc.stats()
+    assert st["schedule"] == 1 and st["batches"] == (len(S) + 63) // 64
+    with gb.BC.from_graph(g, policy="beamer", schedule="grid", streams=1) as bc:
+        bc.compute(S)
+        assert np.array_equal(bc.read_fixed(), fast)
+
+
+def test_rmat18_bench_configuration_against_the_oracle(gb):
+    g, S = gg.workload("rmat18")
+    S = S[:96]  # two batches, so two workers
+    with _bench_handle(gb, g) as bc:
+        bc.compute(S)
+        got = bc.read()
+    want, _ = oracle.bc_graph(g, S)
+    assert_bc_close(got, want)
+
+
 def test_disconnected_isolated_and_duplicate_sources(gb):
     g = gg.from_edges(12, [(0, 1), (1, 2), (2, 3), (4, 5), (5, 6), (6, 4), (8, 9)])  # 7, 10, 11 isolated
     S = np.array([0, 7, 0, 4, 11, 9, 9, 3], np.int32)
