@@ -1,21 +1,41 @@
 """Benchmark: exact Brandes BC throughput in GTEPS (sources x directed edges / s).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat18]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat22]
                     [--policy auto] [--width 64] [--impl ours|reference]
 
-One step = one bc_compute over the workload's whole source list (forward,
-backward and BC accumulation for every source) followed by bc_read of the
-BC vector into device memory; the graph and sources are resident in HBM.
-An L2 flush (a 512 MiB device write) separates timed steps and is not timed.
-Steps are timed with CUDA events on the compute stream.  `e2e` times the same
-metric through the C ABI with host buffers: bc_graph_create from pinned host
-CSR, bc_compute from pinned host sources, bc_read into pinned host memory,
-bc_graph_destroy.  `--impl reference` times the CPU oracle (the plain
-single-threaded Brandes of oracle/) on a bounded sample of the same workload.
+Default workload: R-MAT scale 22 (4,194,304 vertices, 128,304,280 directed
+CSR entries) with 16,384 sources, the configuration on which the learned-
+batched vs plain comparison is stated.  One step = one bc_compute over the
+workload's whole source list (forward, backward and BC accumulation for
+every source) followed by bc_read of the BC vector into device memory; the
+graph and sources are resident in HBM.  An L2 flush (a 512 MiB device
+write) separates timed steps and is not timed.  Steps are timed with CUDA
+events on the compute stream.
 
-With torchrun (N > 1) every rank runs the same workload size on its own
-seeded source sample (weak scaling; no collective on the data path), and
-rank 0 prints the line with the time of the slowest rank.
+Beside the headline the line carries:
+  plain      the plain one-source-at-a-time GPU Brandes (batch width 1,
+             the same handle options) on a seeded sample of the list, timed
+             the same way, with the batched form on the same sample;
+             vs_plain = value / plain.value
+  traversed  GTEPS counting only the edges each source's BFS reaches (the
+             CSR entries of its connected component)
+  e2e        the same metric through the C ABI with host buffers:
+             bc_graph_create from pinned host CSR, bc_compute from pinned
+             host sources, bc_read into pinned host memory, destroy
+  roofline   the dominant step kind's algorithmic bytes over its CUDA-event
+             time (a traced run), against the measured HBM copy peak
+  cpu_baseline  the CPU oracle (oracle/) on a bounded sample, one process
+             per host core, and on one core
+`--impl reference` times the CPU oracle alone on a bounded sample per step.
+
+With torchrun (N > 1) every rank runs the same number of sources, its own
+seeded share of the job's source list (weak scaling), over its own replica
+of the graph; each timed step ends with the one exchange the method has:
+the ranks' exact fixed-point partial BC vectors are all-gathered (NCCL) and
+added into every rank's handle by the library (multirank.reduce_bc), so
+every rank holds the BC of the whole list.  Rank 0 prints the line with the
+time of the slowest rank, and checks outside the timed region that the
+reduced BC of a small sub-list equals one GPU's run over it bit for bit.
 """
 from __future__ import annotations
 
@@ -62,7 +82,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="rmat18", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
     ap.add_argument("--policy", default="auto")
     ap.add_argument("--width", type=int, default=64)
     ap.add_argument("--schedule", default="auto", choices=["auto", "grid", "block", "pair"])
@@ -72,7 +92,10 @@ def parse():
                     help="order sources by the shipped grouping network before packing them into words")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=48, help="sources in the oracle's timed sample")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="sources of the single-core oracle sample (0: sized from the graph, about 10-30 s)")
+    ap.add_argument("--plain-sources", type=int, default=256,
+                    help="sources of the plain one-source-at-a-time arm's seeded sample (0: no plain arm)")
     return ap.parse_args()
 
 
@@ -83,15 +106,23 @@ def dist_env():
     return rank, world, local
 
 
+def rank_sources(g, S, rank):
+    """Rank `rank`'s share of the job's source list: rank 0 takes the
+    workload's list, rank r > 0 another seeded sample of the same size
+    (weak scaling: the job's list is the concatenation of the shares)."""
+    from paper_2008_05718_gb300 import graphgen as gg
+    if rank == 0:
+        return S
+    return gg.sample_sources(g.n, len(S), seed=10_000 + 97 * rank + len(S))
+
+
 def load_workload(name, rank):
-    """(graph, sources, edge weights or None)."""
+    """(graph, sources of this rank, edge weights or None)."""
     from paper_2008_05718_gb300 import graphgen as gg
     base, maxw, wseed = WEIGHTED.get(name, (name, 0, 0))
     g, S = gg.workload(base)
     w = gg.edge_weights(g, maxw, seed=wseed) if maxw else None
-    if rank > 0:  # weak scaling: same count, another seeded sample
-        S = gg.sample_sources(g.n, len(S), seed=10_000 + 97 * rank + len(S))
-    return g, S, w
+    return g, rank_sources(g, S, rank), w
 
 
 def pair_bytes_per_step(n, nnz, k, nb, weighted):
@@ -156,6 +187,17 @@ class ClockSampler:
 
 
 # ---- reference arm: the CPU oracle -------------------------------------------
+# The oracle (oracle/brandes.c, unmodified) runs single-threaded per process;
+# oracle/pool.py runs one process per host core (spawn) over shares of a
+# source sample and sums their BC.  Sample sizes follow the graph's size so
+# that each timed piece stays within seconds: the oracle's cost per source
+# grows with the CSR entries (about 10 s per source on R-MAT 22 and 0.1 s on
+# R-MAT 18 for one core).
+
+def oracle_sources_per_core(nnz, budget_entries):
+    """Sources per core so that one core reads about budget_entries CSR entries."""
+    return int(max(1, min(48, budget_entries // max(nnz, 1))))
+
 
 def cpu_oracle_gteps(g, S, sample, w=None):
     import oracle
@@ -170,76 +212,26 @@ def cpu_oracle_gteps(g, S, sample, w=None):
     return len(src) * g.nnz / dt / 1e9, dt, len(src)
 
 
-# ---- the oracle on every host core: one process per core (spawn: started
-# after CUDA work, a forked child of a CUDA process would hang), each running
-# the unmodified oracle over a share of the sources; BC is summed.
-
-_POOL_GRAPH = None
-
-
-def _pool_init(n, row_ptr, col, weight):
-    global _POOL_GRAPH
-    import oracle
-    oracle.build()
-    _POOL_GRAPH = (n, row_ptr, col, weight)
-
-
-def _pool_bc(sources):
-    import oracle
-    n, rp, col, w = _POOL_GRAPH
-    if w is None:
-        return oracle.bc(n, rp, col, sources)[0]
-    return oracle.bc_weighted(n, rp, col, w, sources)[0]
-
-
-class OraclePool:
-    def __init__(self, g, w, cores):
-        import multiprocessing as mp
-        self.cores = max(1, int(cores))
-        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_pool_init,
-                                                 initargs=(g.n, g.row_ptr, g.col, w))
-        self.pool.map(_pool_bc, [np.zeros(0, np.int32)] * self.cores)  # workers up and the oracle loaded
-
-    def time(self, g, sources):
-        """Seconds to run the oracle over `sources`, split over the workers."""
-        parts = [p for p in np.array_split(np.asarray(sources, np.int32), self.cores) if len(p)]
-        t = time.perf_counter()
-        total = sum(self.pool.map(_pool_bc, parts))
-        dt = time.perf_counter() - t
-        assert total.shape == (g.n,)
-        return dt
-
-    def close(self):
-        self.pool.close()
-        self.pool.join()
-
-
-def host_cores():
-    try:
-        return len(os.sched_getaffinity(0))
-    except AttributeError:
-        return os.cpu_count() or 1
-
-
 def run_reference(args):
+    from oracle.pool import OraclePool, host_cores
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     g, S, w = load_workload(args.workload, 0)
     cores = host_cores()
-    sample = max(1, min(args.cpu_sample // 4 * cores, len(S)))
-    pool = OraclePool(g, w, cores)
+    per = oracle_sources_per_core(g.nnz, 10**8)
+    sample = max(1, min(per * cores, len(S)))
     times = []
-    for i in range(args.warmup + args.steps):
-        lo = i * sample % len(S)
-        src = np.concatenate([S[lo:], S[:lo]])[:sample]
-        dt = pool.time(g, src)
-        if i >= args.warmup:
-            times.append(dt)
-    pool.close()
+    with OraclePool(g, w, cores) as pool:
+        for i in range(args.warmup + args.steps):
+            lo = i * sample % len(S)
+            src = np.concatenate([S[lo:], S[:lo]])[:sample]
+            _, dt = pool.bc(src)
+            if i >= args.warmup:
+                times.append(dt)
     value = args.steps * sample * g.nnz / sum(times) / 1e9
-    desc = (f"{sample} sources per step of the {len(S)}-source list over {cores} processes, full graph "
-            f"(n={g.n}, nnz={g.nnz})")
+    desc = (f"{sample} sources per step ({per} per process) of the {len(S)}-source list over {cores} "
+            f"processes, full graph (n={g.n}, nnz={g.nnz})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -327,10 +319,14 @@ def run_ours(args):
         return gbbc.BC.from_weighted(g.n, rp_, col_, wt_, stream=stream, **kw)
 
     bc = prepare(make(rp, col, wt, **opts))
+    if world > 1:
+        from paper_2008_05718_gb300 import multirank as mr
 
     def step():
         bc.reset()
         bc.compute(src, stream=stream)
+        if world > 1:  # the exchange step: every rank ends with the whole BC
+            mr.reduce_bc(bc, stream=stream, device=dev)
         bc.read(out, stream=stream)
 
     for _ in range(args.warmup):
@@ -359,6 +355,44 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
     value = world * args.steps * k * g.nnz / total_s / 1e9
+    # edges the sources' searches actually reach: each source's component
+    from paper_2008_05718_gb300 import graphgen as gg
+    reach = int(gg.component_entries(g)[S].sum())
+    traversed = {"value": world * args.steps * reach / total_s / 1e9, "unit": UNIT,
+                 "reachable_fraction": reach / (k * g.nnz)}
+
+    def timed(h, sources, steps, warm):
+        """CUDA-event milliseconds per step of reset + compute + read on h
+        (an L2 flush before each timed step, not timed)."""
+        def once():
+            h.reset()
+            h.compute(sources, stream=stream)
+            h.read(out, stream=stream)
+        for _ in range(warm):
+            once()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_((i + 7) & 0xFF)
+            evs[i][0].record(stream)
+            once()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+    # ---- the plain one-source-at-a-time GPU path on a seeded sample ----
+    plain = None
+    if args.plain_sources > 0 and wts is None and args.width != 1:
+        kp = min(args.plain_sources, k)
+        sp = torch.from_numpy(gg.sample_sources(k, kp, seed=4242)).to(dev)
+        sp = src[sp.long()].contiguous()  # a seeded sample of the list itself
+        p_steps = max(1, min(args.steps, 3))
+        with make(rp, col, None, **dict(opts, batch_width=1)) as hp:
+            ms_plain = timed(hp, sp, p_steps, 1)
+        ms_batched = timed(bc, sp, p_steps, 1)
+        plain = {"value": kp * g.nnz / (ms_plain / 1e3) / 1e9, "unit": UNIT, "sources": kp, "steps": p_steps,
+                 "ms_per_step": ms_plain, "sample": "seeded uniform sample (seed 4242) of the source list",
+                 "batched_on_sample": {"value": kp * g.nnz / (ms_batched / 1e3) / 1e9, "ms_per_step": ms_batched}}
 
     # ---- end to end through the C ABI with host buffers ----
     rp_h = torch.from_numpy(g.row_ptr).pin_memory()
@@ -413,17 +447,35 @@ def run_ours(args):
                           "GBps": step_bytes / total_s * args.steps / 1e9,
                           "frac": step_bytes / total_s * args.steps / 1e9 / peak}
 
+    # ---- N > 1: the reduced BC of a sub-list against one GPU, bit for bit ----
+    mcheck = None
+    if world > 1:
+        sub = 64
+        with prepare(make(rp, col, wt, **opts)) as hs:
+            hs.compute(src[:sub], stream=stream)
+            mr.reduce_bc(hs, stream=stream, device=dev)
+            red = hs.read_fixed()
+        if rank == 0:
+            allsub = np.concatenate([rank_sources(g, S, r)[:sub] for r in range(world)])
+            with prepare(make(rp, col, wt, **opts)) as h1:
+                h1.compute(allsub, stream=stream)
+                one = h1.read_fixed()
+            mcheck = {"sources": int(len(allsub)), "bit_identical": bool(np.array_equal(red, one))}
+
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        val1, dt1, ks1 = cpu_oracle_gteps(g, S, min(args.cpu_sample, k), wts)
+        from oracle.pool import OraclePool, host_cores
+        one = args.cpu_sample or oracle_sources_per_core(g.nnz, 4 * 10**8)
+        val1, dt1, ks1 = cpu_oracle_gteps(g, S, min(one, k), wts)
         cores = host_cores()
-        ks = min(args.cpu_sample * cores, k)
-        pool = OraclePool(g, wts, cores)
-        dt = pool.time(g, S[:ks])
-        pool.close()
+        per = oracle_sources_per_core(g.nnz, 4 * 10**8)
+        ks = min(per * cores, k)
+        with OraclePool(g, wts, cores) as pool:
+            _, dt = pool.bc(S[:ks])
         cpu = {"value": ks * g.nnz / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {ks} of the {k} sources over {cores} processes, full graph; {dt:.1f} s",
+               "sample": f"first {ks} of the {k} sources over {cores} processes ({per} each), full graph; "
+                         f"{dt:.1f} s",
                "single_core": {"value": val1, "sources": ks1, "seconds": round(dt1, 2)}}
 
     if rank == 0:
@@ -437,7 +489,8 @@ def run_ours(args):
                            "schedule": ["auto", "grid", "block", "pair"][st_all["schedule"]],
                            "l2": "flushed between timed steps (512 MiB device write)"},
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
+                "plain": plain, "vs_plain": (value / world / plain["value"]) if plain else None,
+                "traversed": traversed, "multi_gpu_check": mcheck, "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
                 "step_ms": [round(x, 3) for x in step_ms]}
         print(json.dumps(line))
     bc.close()

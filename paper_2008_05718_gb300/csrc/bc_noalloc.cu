@@ -7,16 +7,26 @@
 // All per-batch working state lives in one file-scope device array,
 // g_noalloc_scratch, sized for kNoallocMaxVertices vertices.  It is part of
 // the library image: every GPU that loads libgbbc.so holds it until the
-// process exits.  Every call shares it, so two calls whose work overlaps on
-// the GPU (different streams, or several host threads) race and give wrong
-// results; serialise them.  The array keeps the previous call's contents:
+// process exits.  Every call shares it, so two calls whose work overlapped on
+// the GPU would race and give wrong results.  The library rules that out
+// within one process: calls on one device hold a per-device host lock for
+// their whole duration, and each call returns only after its work on the
+// stream has finished.  The array keeps the previous call's contents:
 // everything a batch needs at zero is cleared at the start of that batch.
+// The host-side level boundaries of a batch live in a static per-device
+// array too (not on the caller's stack, which may be small), used under the
+// same lock.
 //
 // Host code cannot use the array's name as a device address (in host code
 // the symbol is a host-side stand-in), so the device address is looked up
 // with cudaGetSymbolAddress once per device, the first time a call runs on
-// that device with it current.  That first call should therefore come before
-// any stream capture begins.
+// that device with it current.
+//
+// Each call first checks the caller's CSR on the device (row bounds, column
+// range, sorted rows without duplicates or self-loops, symmetry) with the
+// library's validation kernel, writing its flags into a word of the scratch,
+// so that no later kernel reads or writes outside the caller's arrays or the
+// scratch.
 //
 // The kernels are the same ones bc_compute launches (64 sources per batch);
 // this path always expands top-down, keeps this call's BC in the scratch's
@@ -56,7 +66,8 @@ constexpr long long kOffHcarry = kOffHacc + align256(16 * kLanes * kNoallocMaxVe
 constexpr long long kOffTasks = kOffHcarry + align256(8 * kNoallocMaxVertices);
 constexpr long long kOffCtr = kOffTasks + align256(8 * kNoallocTcap);
 constexpr long long kOffSrc = kOffCtr + align256((long long)sizeof(Counters));
-constexpr long long kScratchBytes = kOffSrc + align256(4 * kLanes);
+constexpr long long kOffFlags = kOffSrc + align256(4 * kLanes);  // validation flags
+constexpr long long kScratchBytes = kOffFlags + align256(4);
 static_assert(kScratchBytes < (64ll << 20), "no-allocation scratch above 64 MiB");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -64,6 +75,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_ptr[kMaxDevices] = {nullptr};
+// Per device: the lock that serialises calls, and the level boundaries of
+// the batch in flight (static storage: untouched pages cost no memory).
+std::mutex g_call_mutex[kMaxDevices];
+long long g_level_off[kMaxDevices][kNoallocMaxVertices + 2];
 
 // Device address of the scratch array on the current device (set-up on the
 // first call per device).
@@ -114,7 +129,10 @@ extern "C" gbbc_status bc_compute_noalloc(int32_t n, int64_t nnz, const int32_t*
     NA_CK(scratch_address(&base));
     int dev = 0, nsm = 152;
     NA_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return GBBC_ERR_CUDA;
     NA_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    std::lock_guard<std::mutex> call_lock(g_call_mutex[dev]);
+    long long* off = g_level_off[dev];  // level boundaries of a batch
 
     Slot s;
     s.n = n;
@@ -141,9 +159,24 @@ extern "C" gbbc_status bc_compute_noalloc(int32_t n, int64_t nnz, const int32_t*
     // F is indexed [parity][n] with the stride of this graph's n
     Csr c{n, (long long)nnz, row_ptr, col};
     const int heavy_deg = 1024;
-    long long off[kNoallocMaxVertices + 2];  // level boundaries of a batch (on the stack)
     const size_t disc_off = offsetof(Counters, heavy), disc_bytes = offsetof(Counters, err) - disc_off;
     const size_t gath_off = offsetof(Counters, lane_sum), gath_bytes = offsetof(Counters, medium) - gath_off;
+
+    // The caller's CSR: row_ptr[0] = 0 and row_ptr[n] = nnz, then the device
+    // check of every row (flags in the scratch; any flag rejects the graph).
+    int32_t ends[2] = {-1, -1};
+    NA_CK(cudaMemcpyAsync(&ends[0], row_ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NA_CK(cudaMemcpyAsync(&ends[1], row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NA_CK(cudaStreamSynchronize(st));
+    if (ends[0] != 0 || (long long)ends[1] != (long long)nnz) return GBBC_ERR_INVALID;
+    int32_t* d_flags = (int32_t*)(base + kOffFlags);
+    NA_CK(cudaMemsetAsync(d_flags, 0, sizeof(int32_t), st));
+    launch_validate(c, d_flags, st);
+    NA_CK(cudaGetLastError());
+    int32_t flags = 0;
+    NA_CK(cudaMemcpyAsync(&flags, d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NA_CK(cudaStreamSynchronize(st));
+    if (flags) return GBBC_ERR_INVALID;
 
     NA_CK(cudaMemsetAsync(bc_fixed, 0, 2 * (size_t)n * sizeof(u64), st));
     // heavy-row accumulators must start at zero (they are left at zero by

@@ -57,6 +57,8 @@ def _load():
                                     ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, P(_CSR)]
             lib.gg_grid.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, P(_CSR)]
             lib.gg_lcc.argtypes = [P(_CSR), P(_CSR), i32p]
+            lib.gg_components.argtypes = [P(_CSR), i32p]
+            lib.gg_components.restype = ctypes.c_int32
             lib.gg_tri.argtypes = [ctypes.c_int32, ctypes.c_uint64, P(_CSR)]
             lib.gg_weights.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_uint64, i32p]
             lib.gg_rgg.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, P(_CSR)]
@@ -244,6 +246,24 @@ def largest_cc(g: Graph) -> tuple[Graph, np.ndarray]:
         raise MemoryError("gg_lcc failed")
     out = _take(c, g.name + "_lcc")
     return out, old[: out.n].copy()
+
+
+def component_labels(g: Graph) -> np.ndarray:
+    """Connected-component label of every vertex (labels numbered from the
+    smallest vertex id)."""
+    src = _CSR(g.n, g.nnz, _i32p(g.row_ptr), _i32p(g.col))
+    comp = np.zeros(max(g.n, 1), np.int32)
+    if _load().gg_components(ctypes.byref(src), _i32p(comp)) < 0:
+        raise MemoryError("gg_components failed")
+    return comp[: g.n].copy()
+
+
+def component_entries(g: Graph) -> np.ndarray:
+    """For every vertex, the CSR entries (directed edges) of its connected
+    component: the edges a BFS from that vertex traverses."""
+    comp = component_labels(g)
+    per = np.bincount(comp, weights=np.diff(g.row_ptr).astype(np.float64), minlength=int(comp.max(initial=-1)) + 1)
+    return per[comp].astype(np.int64)
 
 
 def sample_sources(n: int, k: int, seed: int) -> np.ndarray:

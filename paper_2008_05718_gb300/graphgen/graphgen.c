@@ -242,6 +242,18 @@ static int32_t components(const gg_csr *g, int32_t *comp, int32_t *queue) {
     return nc;
 }
 
+/* Component label of every vertex (comp[n], labels in discovery order from
+ * the smallest vertex id).  Returns the number of components, -1 when out
+ * of memory. */
+int32_t gg_components(const gg_csr *g, int32_t *comp) {
+    if (g->n == 0) return 0;
+    int32_t *queue = (int32_t *)malloc((size_t)g->n * sizeof(int32_t));
+    if (!queue) return -1;
+    int32_t nc = components(g, comp, queue);
+    free(queue);
+    return nc;
+}
+
 /* Largest connected component (ties: the one holding the smallest id), with
  * vertices relabelled compactly in increasing old-id order. old_id (optional,
  * n entries) receives the old id of each kept vertex. */

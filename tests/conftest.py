@@ -3,6 +3,8 @@
 Markers:
   gpu   needs a CUDA device and the compiled CUDA library (run with -m gpu)
   slow  CPU tests that take more than a few seconds
+  scale GPU parity at full benchmark size against the oracle on every host
+        core (minutes; part of -m gpu)
 """
 import os
 import sys
@@ -17,6 +19,7 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU and libgbbc.so")
     config.addinivalue_line("markers", "slow: CPU test that takes more than a few seconds")
+    config.addinivalue_line("markers", "scale: full-size GPU parity against the multi-core oracle")
 
 
 @pytest.fixture(scope="session")
