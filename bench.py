@@ -253,20 +253,30 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("bc_kernels.cu", "bc_persist.cu", "bc_rows.cuh", "bc_fixed.cuh", "bc_internal.cuh")
+
+
+def kernel_source_hash():
+    """SHA-256 (16 hex digits) of the kernel sources an ncu summary covers."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2008_05718_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profiles(kernel_kind, workload, grouping):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source with the same source grouping (else None)."""
+    on the current kernel sources with the same source grouping (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_kind}_{workload}.txt")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_2008_05718_gb300", "csrc", "bc_kernels.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha256_16") != h or vals.get("source_grouping", "list order") != grouping:
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash() or \
+            vals.get("source_grouping", "list order") != grouping:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])

@@ -1,17 +1,19 @@
 """Sharding sources over ranks and combining their BC exactly.
 
 Sources are independent (Eq. 2: BC is a sum over sources), so each rank runs
-bc_compute on its own share and only the final BC vectors are combined.  The
-library keeps BC as 128-bit unsigned fixed point (units 2^-64, bc_read_fixed);
-adding those integers is exact and order-free, so any split of the sources
-gives the same bits as one GPU over all of them.  Rounding to FP64 happens
-once, after the sum.
+bc_compute on its own share of the source list over its own replica of the
+graph, and only the final BC vectors are combined: one exchange step.  The
+library keeps BC as 128-bit unsigned fixed point (units 2^-64); each rank
+reads its partial in that form into device memory (bc_read_fixed), the
+partials are all-gathered over the process group (NCCL between GPUs: each
+rank receives copies in its own memory, no peer loads and no multicast), and
+each rank adds the other ranks' partials into its handle with bc_add_fixed,
+the library's exact integer adds.  Any split of the sources therefore gives
+the bits one GPU over all of them would give; bc_read rounds to FP64 once.
 """
 from __future__ import annotations
 
 import numpy as np
-
-MASK64 = (1 << 64) - 1
 
 
 def shard(sources, rank: int, world: int):
@@ -23,36 +25,29 @@ def shard(sources, rank: int, world: int):
     return S[lo:hi]
 
 
-def add_fixed(a, b):
-    """Exact sum of two [n, 2] uint64 (low, high) fixed-point vectors."""
-    a = np.asarray(a, np.uint64)
-    b = np.asarray(b, np.uint64)
-    lo = a[:, 0] + b[:, 0]
-    carry = (lo < a[:, 0]).astype(np.uint64)
-    hi = a[:, 1] + b[:, 1] + carry
-    return np.stack([lo, hi], axis=1)
-
-
-def sum_fixed(parts):
-    out = np.zeros_like(np.asarray(parts[0], np.uint64))
-    for p in parts:
-        out = add_fixed(out, p)
-    return out
-
-
-def fixed_to_double(f):
-    """Correctly rounded FP64 of 128-bit fixed point (units 2^-64)."""
-    f = np.asarray(f, np.uint64)
-    return np.array([float((int(h) << 64) | int(l)) / 18446744073709551616.0 for l, h in f], np.float64)
-
-
-def allreduce_fixed(fixed, group=None):
-    """Exact sum over the ranks of a torch.distributed group (any backend):
-    gather every rank's vector, add in rank order with carries."""
+def allgather_fixed(local, group=None):
+    """Every rank's fixed-point vector (a torch int64 tensor of 2n words,
+    on the rank's device for NCCL or on the host for gloo), in rank order."""
     import torch
     import torch.distributed as dist
     world = dist.get_world_size(group)
-    t = torch.from_numpy(np.ascontiguousarray(fixed, np.uint64).view(np.int64))
-    parts = [torch.empty_like(t) for _ in range(world)]
-    dist.all_gather(parts, t, group=group)
-    return sum_fixed([p.numpy().view(np.uint64) for p in parts])
+    parts = [torch.empty_like(local) for _ in range(world)]
+    dist.all_gather(parts, local.contiguous(), group=group)
+    return parts
+
+
+def reduce_bc(bc, group=None, stream=None, device=None):
+    """Add every other rank's partial BC into `bc` (a gbbc.BC handle) so that
+    each rank's handle holds the sum over all ranks' sources; returns the
+    gathered partials (rank order)."""
+    import torch
+    import torch.distributed as dist
+    rank = dist.get_rank(group)
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    mine = torch.empty(2 * bc.n, dtype=torch.int64, device=dev)
+    bc.read_fixed_into(mine, stream=stream)
+    parts = allgather_fixed(mine, group)
+    for r, p in enumerate(parts):
+        if r != rank:
+            bc.add_fixed(p, stream=stream)
+    return parts

@@ -1,5 +1,5 @@
-"""Host logic of bench.py (no GPU): the committed DRAM-traffic summary is tied
-to the current kernel source, the pair kernel's bytes model, the weighted
+"""Host logic of bench.py (no GPU): DRAM traffic is reported only from an ncu
+summary of the current kernel sources, the pair kernel's bytes model, the weighted
 workloads, and the reference arm's JSON line."""
 import hashlib
 import json
@@ -14,23 +14,24 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_traffic_summary_matches_the_kernel_source():
-    # bench.py only reports the committed ncu traffic when it was taken on the
-    # current kernels with the bench's grouping: a kernel edit without a new
-    # capture shows up here
-    src = os.path.join(ROOT, "paper_2008_05718_gb300", "csrc", "bc_kernels.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    vals = {}
-    for line in open(os.path.join(ROOT, "profiles", "backward_rmat18.txt")):
-        if ":" in line:
-            k, v = line.split(":", 1)
-            vals[k.strip()] = v.strip()
-    assert vals["kernel_source_sha256_16"] == sha
-    assert vals["source_grouping"] == "learned"
-    t = bench.traffic_from_profiles("backward", "rmat18", "learned")
-    assert t is not None and t > float(vals["algorithmic_bytes_per_launch_in_bench"])
-    assert bench.traffic_from_profiles("backward", "rmat18", "list order") is None
-    assert bench.traffic_from_profiles("gather", "rmat18", "learned") is None
+def test_traffic_is_reported_only_from_a_summary_of_the_current_kernels(tmp_path, monkeypatch):
+    # bench.py reports ncu DRAM traffic only from a committed summary taken on
+    # the current kernel sources with the bench's source grouping; any kernel
+    # edit without a new capture gives null
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    csrc = tmp_path / "paper_2008_05718_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for name in bench.KERNEL_SOURCES:
+        (csrc / name).write_text("kernel " + name)
+    (tmp_path / "profiles").mkdir()
+    sha = bench.kernel_source_hash()
+    (tmp_path / "profiles" / "persistent_rmat18.txt").write_text(
+        f"kernel_source_sha256_16: {sha}\nsource_grouping: learned\ndram_bytes_per_launch: 123.0\n")
+    assert bench.traffic_from_profiles("persistent", "rmat18", "learned") == 123.0
+    assert bench.traffic_from_profiles("persistent", "rmat18", "list order") is None
+    assert bench.traffic_from_profiles("persistent", "rmat22", "learned") is None
+    (csrc / bench.KERNEL_SOURCES[0]).write_text("edited")
+    assert bench.traffic_from_profiles("persistent", "rmat18", "learned") is None
 
 
 def test_pair_bytes_model():

@@ -136,7 +136,7 @@ def test_learned_policy_requires_weights(gb):
 def test_shipped_policy_gains_over_threshold_rule_on_held_out_traces(gb):
     # held-out graphs (seeds not used in training): both directions timed at
     # every level, so each schedule's cost is exact; the trained network must
-    # not lose to the threshold rule and should sit near the per-level best
+    # be no slower than the threshold rule and sit near the per-level best
     from paper_2008_05718_gb300 import graphgen as gg, policy
     p = policy.shipped_weights()
     assert p is not None and len(p) == gb.bc_mlp_param_count(2)
@@ -144,5 +144,5 @@ def test_shipped_policy_gains_over_threshold_rule_on_held_out_traces(gb):
     tr = policy.collect(graphs, sources=128, seed=4244)
     c = policy.costs(p, tr)
     print("held-out step costs (ms):", c)
-    assert c["learned"] <= 1.02 * c["threshold"]
+    assert c["learned"] <= c["threshold"]
     assert c["learned"] <= 1.10 * c["best"]
