@@ -90,6 +90,8 @@ def parse():
                     help="batches the grid schedule runs at once (0: the library's default)")
     ap.add_argument("--grouping", default="learned", choices=["learned", "none"],
                     help="order sources by the shipped grouping network before packing them into words")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="grid schedule: drive the level loop from the host instead of the persistent kernel")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0,
@@ -305,7 +307,8 @@ def run_ours(args):
     src = torch.from_numpy(S).to(dev)
     out = torch.zeros(g.n, dtype=torch.float64, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    opts = dict(batch_width=args.width, policy=args.policy, streams=args.streams, schedule=args.schedule)
+    opts = dict(batch_width=args.width, policy=args.policy, streams=args.streams, schedule=args.schedule,
+                flags=gbbc.GBBC_HOST_LOOP if args.host_loop else 0)
 
     weights = None
     if args.policy in ("auto", "learned") and args.width != 1:
@@ -342,7 +345,8 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    launches0 = bc.stats()["kernel_launches"]
+    stats0 = bc.stats()
+    launches0 = stats0["kernel_launches"]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
@@ -357,7 +361,10 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clocks = clk.summary()
-    launches = bc.stats()["kernel_launches"] - launches0
+    stats1 = bc.stats()
+    launches = stats1["kernel_launches"] - launches0
+    p_launches = stats1["persist_launches"] - stats0["persist_launches"]
+    p_ms = stats1["persist_ms"] - stats0["persist_ms"]
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
     if world > 1:
@@ -427,7 +434,7 @@ def run_ours(args):
     # ---- roofline of the dominant step kind (one traced step) ----
     st_all = bc.stats()
     if wts is None and st_all["schedule"] != 3:
-        with make(rp, col, None, flags=gbbc.GBBC_TRACE, **opts) as tb:
+        with make(rp, col, None, **dict(opts, flags=opts["flags"] | gbbc.GBBC_TRACE)) as tb:
             prepare(tb)
             tb.compute(src, stream=stream)
             tb.sync()
@@ -437,22 +444,40 @@ def run_ours(args):
         nb = st_all["batches"] // max(1, args.warmup + args.steps)
         prof = {"pair": {"ms": ms, "launches": 1,
                          "bytes": pair_bytes_per_step(g.n, g.nnz, k, nb, wts is not None)}}
-    kind = max(prof, key=lambda x: prof[x]["ms"])
-    p = prof[kind]
     peak, peak_src = measured_peaks()
-    achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] > 0 else 0.0
-    tr = traffic_from_profiles(kind, args.workload, "learned" if gweights is not None else "list order")
+    grouping_name = "learned" if gweights is not None else "list order"
     total_ms = sum(v["ms"] for v in prof.values())
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": tr, "kernel": kind, "launches_per_step": p["launches"],
-            "bytes_per_launch": p["bytes"] / max(p["launches"], 1), "ms_per_launch": p["ms"] / max(p["launches"], 1),
-            "share_of_step": p["ms"] / total_ms if total_ms else None, "peak_source": f"{peak_src} hbm_gbs (copy)",
-            "steps": {x: {"ms": round(v["ms"], 3), "GBps": (v["bytes"] / v["ms"] / 1e6) if v["ms"] else 0.0}
-                      for x, v in prof.items()}}
-    # the whole step in the timed region: every step kind's algorithmic bytes
-    # (from the traced step, whose batches run one at a time) over the timed
-    # step time (batches overlap there, on several streams)
     step_bytes = sum(v["bytes"] for v in prof.values())
+    steps_ctx = {x: {"ms": round(v["ms"], 3), "GBps": (v["bytes"] / v["ms"] / 1e6) if v["ms"] else 0.0,
+                     "bytes": v["bytes"]} for x, v in prof.items()}
+    if p_launches > 0:
+        # the persistent grid-schedule kernel runs every level step of every
+        # batch: its algorithmic bytes per launch are the whole step's (every
+        # step kind's compulsory bytes, from a traced run of the same
+        # batches and directions) over its CUDA-event duration in the timed
+        # region
+        per_launch_bytes = step_bytes * args.steps / p_launches
+        ms_launch = p_ms / p_launches
+        achieved = per_launch_bytes / (ms_launch / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_from_profiles("persistent", args.workload, grouping_name),
+                "kernel": "k_persist", "launches_per_step": p_launches / args.steps,
+                "bytes_per_launch": per_launch_bytes, "ms_per_launch": ms_launch,
+                "share_of_step": p_ms / (1e3 * total_s), "peak_source": f"{peak_src} hbm_gbs (copy)",
+                "slots": stats1["persist_slots"], "blocks": stats1["persist_blocks"],
+                "steps": steps_ctx}
+    else:
+        kind = max(prof, key=lambda x: prof[x]["ms"])
+        p = prof[kind]
+        achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] > 0 else 0.0
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_from_profiles(kind, args.workload, grouping_name), "kernel": kind,
+                "launches_per_step": p["launches"], "bytes_per_launch": p["bytes"] / max(p["launches"], 1),
+                "ms_per_launch": p["ms"] / max(p["launches"], 1),
+                "share_of_step": p["ms"] / total_ms if total_ms else None,
+                "peak_source": f"{peak_src} hbm_gbs (copy)", "steps": steps_ctx}
+    # the whole step in the timed region: every step kind's algorithmic bytes
+    # over the timed step time
     roof["timed_step"] = {"algorithmic_bytes": step_bytes, "ms": 1e3 * total_s / args.steps,
                           "GBps": step_bytes / total_s * args.steps / 1e9,
                           "frac": step_bytes / total_s * args.steps / 1e9 / peak}

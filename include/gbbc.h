@@ -69,10 +69,15 @@ enum gbbc_flags {
                                   bc_compute for bc_read_source_state */
     GBBC_TRACE = 1u << 1,      /* record per-level features and CUDA-event
                                   times (bc_get_trace, bc_get_profile) */
-    GBBC_TRACE_BOTH = 1u << 2  /* with GBBC_TRACE: time both directions at
+    GBBC_TRACE_BOTH = 1u << 2, /* with GBBC_TRACE: time both directions at
                                   every forward level (the step is run top-down,
                                   undone, then run bottom-up); results are
                                   unchanged, only slower */
+    GBBC_HOST_LOOP = 1u << 3   /* grid schedule: drive the level loop from the
+                                  host (per-step kernels, a counter read-back
+                                  per level, concurrent batches on host
+                                  threads) instead of the persistent kernel,
+                                  as tracing and kept state do; same bits */
 };
 
 typedef struct gbbc_options {
@@ -82,7 +87,13 @@ typedef struct gbbc_options {
     int32_t policy;        /* enum gbbc_policy */
     int32_t validate;      /* 1: check CSR symmetry, sorted rows, no loops or
                               duplicates on the device at create time */
-    int64_t timeout_spins; /* bound on any device-side wait; 0 = default */
+    int64_t timeout_spins; /* bound on any device-side wait, in polls of the
+                              waited-for word (a poll takes about 0.1 us):
+                              a grid barrier of the persistent grid schedule
+                              that waits longer gives up, every block of the
+                              launch returns, and the call fails with
+                              GBBC_ERR_TIMEOUT (the handle's BC is then
+                              undefined until bc_reset); 0 = default, 10^8 */
     uint32_t flags;        /* enum gbbc_flags */
     int32_t heavy_degree;  /* rows longer than this are processed by a whole
                               thread block; 0 = default */
@@ -108,8 +119,14 @@ enum gbbc_schedule {
                                 GPU, else the first call times some batches in
                                 both modes (results kept) and the faster mode
                                 is kept for the handle */
-    GBBC_SCHEDULE_GRID = 1,  /* one batch at a time on the whole GPU, a kernel
-                                per level step, host read-back per level */
+    GBBC_SCHEDULE_GRID = 1,  /* batches on the whole GPU: one persistent
+                                cooperative launch per call runs up to
+                                `streams` batches at once (8 by default), each
+                                batch one level step per tick, the level loop
+                                on the device between grid-wide barriers;
+                                with tracing, kept state or GBBC_HOST_LOOP
+                                the host drives the loop instead (a kernel
+                                per level step, a read-back per level) */
     GBBC_SCHEDULE_BLOCK = 2, /* one thread-block cluster (1 to 8 blocks) per
                                 batch, many batches at once, one persistent
                                 launch per call; the level loop runs on the
@@ -186,6 +203,21 @@ gbbc_status bc_read(gbbc_graph* g, double* bc_out, int32_t graph_id, void* strea
 gbbc_status bc_read_fixed(gbbc_graph* g, uint64_t* out, int32_t graph_id, void* stream);
 
 /*
+ * Add a BC vector in the exact internal form (2 * n uint64 values as
+ * bc_read_fixed gives them; host or device) into the handle's accumulated
+ * BC: the whole vector when graph_id == -1, else graph graph_id's entries.
+ * The adds are 128-bit integer adds with carry, exact and independent of
+ * order, so partial results over disjoint source sets (computed by other
+ * GPUs or other handles of the same graph, Eq. 2 being a sum over sources)
+ * combine into exactly the bits one handle over all the sources holds;
+ * bc_read then rounds the total to FP64 once.  Enqueued on `stream` and
+ * synchronised before returning.
+ * Errors: GBBC_ERR_INVALID (NULL partial, bad graph_id), GBBC_ERR_OOM (a
+ * host partial needs a device staging buffer), GBBC_ERR_CUDA.
+ */
+gbbc_status bc_add_fixed(gbbc_graph* g, const uint64_t* partial, int32_t graph_id, void* stream);
+
+/*
  * Per-source state of the last bc_compute, for sources in that call when
  * GBBC_KEEP_STATE was set: dist (int32[n], -1 unreachable), sigma (uint64[n],
  * number of shortest paths mod 2^64), overflow (uint8[n], 1 iff the true
@@ -227,6 +259,11 @@ typedef struct gbbc_stats {
     int32_t schedule;       /* schedule of the last call (after autotuning;
                                0 when it mixed both) */
     int32_t block_slots;    /* concurrent batches of the block schedule */
+    int64_t persist_launches; /* launches of the persistent grid-schedule kernel */
+    double persist_ms;      /* their summed duration (CUDA events recorded on
+                               the launch stream around each launch) */
+    int32_t persist_slots;  /* batches in flight in the last such launch */
+    int32_t persist_blocks; /* its cooperative grid */
 } gbbc_stats;
 
 gbbc_status bc_get_stats(const gbbc_graph* g, gbbc_stats* out);
@@ -381,30 +418,105 @@ gbbc_status bc_grouping_load(gbbc_graph* g, const float* params, size_t bytes);
 gbbc_status bc_grouping_scores(gbbc_graph* g, const int32_t* sources, int64_t k, float* out, void* stream);
 
 /*
+ * The partitioned method (Sec. IV and Sec. V-A).  The paper splits a graph
+ * too large for one device into a CPU part and a GPU part; here the P parts
+ * live on one GPU, and the method reaches exactly the results of
+ * bc_compute.  A border edge joins two parts; its end points are border
+ * nodes.
+ *
+ * bc_partition: part[v] in [0, P) for each of the handle's n vertices (host
+ * or device int32), or part == NULL for P contiguous ranges of vertex ids.
+ * Builds, once, the intra-part graph (border edges removed), the border
+ * edges, the border nodes of every part (by part, then vertex id), and the
+ * border matrices (Sec. IV-B): BM_p[i][j] = length of a shortest path from
+ * border node i to border node j of part p inside p (-1: none), and
+ * sigmaM_p[i][j] = the number of such paths (Sec. V-A), by BFS inside the
+ * part from every border node.  Single-graph, unweighted handles only.
+ * Errors: GBBC_ERR_INVALID (weighted or multi-graph handle, P, part values),
+ * GBBC_ERR_OOM (the border matrices, sum of |B_p|^2 entries, do not fit).
+ */
+gbbc_status bc_partition(gbbc_graph* g, const int32_t* part, int32_t P, void* stream);
+
+typedef struct gbbc_partition_info {
+    int32_t parts;             /* P (0: not partitioned) */
+    int64_t border_nodes;      /* over all parts */
+    int64_t border_edges;      /* CSR entries joining two parts */
+    int64_t intra_entries;     /* CSR entries inside parts */
+    int64_t matrix_entries;    /* sum over parts of |B_p|^2 */
+    int64_t refinement_sweeps; /* Steps 2-5 sweeps of the last bc_compute_partitioned */
+} gbbc_partition_info;
+
+gbbc_status bc_partition_info(const gbbc_graph* g, gbbc_partition_info* out);
+
+/* Part p's border-node count (*nodes = |B_p|, host), border nodes
+ * (int32[|B_p|], sorted vertex ids), BM (int32, row-major |B_p| x |B_p|),
+ * sigmaM mod 2^64 (uint64) and its overflow flags (uint8: 1 when the count
+ * is >= 2^64); any pointer may be NULL; host or device buffers.
+ * Errors: GBBC_ERR_STATE (no partition), GBBC_ERR_INVALID. */
+gbbc_status bc_read_border_matrix(gbbc_graph* g, int32_t p, int64_t* nodes, int32_t* border, int32_t* bm,
+                                  uint64_t* sigma_m, uint8_t* overflow);
+
+/*
+ * bc_compute by the partitioned method (after bc_partition), per batch of
+ * 64 sources in list order:
+ *   Step 1     BFS with sigma from each source inside its part (Sec. IV-C);
+ *   Steps 2-5  the border nodes' distances refined over the border edges
+ *              (Steps 2, 4) and the border matrices (Steps 3, 5), in sweeps
+ *              over all parts until no distance changes;
+ *   sigma      of every border node b: the paths that stay in the source's
+ *              part (Step 1's count, when Step 1 found the final distance)
+ *              plus, for each border node b' of b's part, the paths whose
+ *              last border edge enters at b' (the sum of sigma over the
+ *              border neighbours of b' one level up) times sigmaM[b'][b]
+ *              when BM[b'][b] closes the distance (Sec. V-A);
+ *   Step 6     relaxation: BFS inside every part from the source and from
+ *              the border nodes entering at their refined distances with
+ *              those counts, giving every vertex its distance and sigma;
+ * then the backward phase (Eq. 2) over the whole graph.  dist and sigma (mod
+ * 2^64, with the overflow flag) equal bc_compute's bit for bit, and so does
+ * BC while counts stay below 2^64 (beyond, the wide counts are products
+ * rounded to 64-bit mantissas: BC agrees to rounding).  GBBC_KEEP_STATE
+ * keeps per-source state as for bc_compute.  Sources are not reordered and
+ * the grid schedule's host loop runs each step.
+ * Errors: GBBC_ERR_STATE (no partition), GBBC_ERR_INVALID, GBBC_ERR_CAPACITY,
+ * GBBC_ERR_OOM, GBBC_ERR_CUDA.
+ */
+gbbc_status bc_compute_partitioned(gbbc_graph* g, const int32_t* sources, int64_t k, void* stream);
+
+/*
  * bc_compute_noalloc - BC of one small graph with no memory allocation.
  * The paper has no counterpart; this entry point exists for callers that
  * must not allocate memory themselves (code running under a pool allocator
  * that owns the whole device, plug-in hosts whose allocator may not be
  * bypassed, real-time loops that cannot afford cudaMalloc's implicit
  * synchronisation).  It calls no cudaMalloc/cudaFree and no allocating
- * library routine, and creates no handle.
+ * library routine, creates no handle and keeps nothing on the caller's
+ * stack beyond a few words (worker threads of plug-in hosts often have
+ * small stacks).
  *
  * Working state lives in one static device array of the library, sized for
  * GBBC_NOALLOC_MAX_VERTICES vertices (about 48 MiB); every GPU that loads
- * libgbbc.so holds it until the process exits.  All calls share it: calls
- * whose work overlaps on the GPU race and must be serialised by the caller.
- * The array keeps the previous call's contents; each batch clears what must
- * start at zero.  The first call on a device looks up the array's device
- * address with cudaGetSymbolAddress (once per device, with that device
- * current), so make it before any stream capture begins.
+ * libgbbc.so holds it until the process exits.  All calls share it, so the
+ * work of two calls must never overlap on the GPU: the library serialises
+ * calls on one device with a host lock held for the whole call, and a call
+ * returns only after its work on `stream` has finished.  The array keeps the
+ * previous call's contents; each call and each batch clears what must start
+ * at zero.  The first call on a device looks up the array's device address
+ * with cudaGetSymbolAddress (once per device, with that device current).
+ * The call synchronises `stream` and copies between pageable host memory
+ * and the device, so it must not be called while `stream` (or the legacy
+ * default stream) is being captured into a CUDA graph.
  *
  * Inputs: n <= GBBC_NOALLOC_MAX_VERTICES vertices; row_ptr[n+1], col[nnz]
  * and bc_out[n] in DEVICE memory; sources[k] in HOST memory, each in [0, n).
+ * The CSR must be symmetric with sorted rows and no self-loops or duplicate
+ * entries, and row_ptr[0] = 0, row_ptr[n] = nnz: every call checks this on
+ * the device (in the static array) before any other kernel reads col.
  * The dependencies of the k sources are ADDED into bc_out (zero it first for
- * plain BC), in 64-source batches, always expanding top-down.  The call
- * returns after the work has finished on `stream`.
- * Errors: GBBC_ERR_CAPACITY when n exceeds GBBC_NOALLOC_MAX_VERTICES (or a
- * shortest-path count reaches 2^64), GBBC_ERR_INVALID for bad arguments or
+ * plain BC), in 64-source batches, always expanding top-down.
+ * Errors: GBBC_ERR_CAPACITY when n exceeds GBBC_NOALLOC_MAX_VERTICES or a
+ * shortest-path count reaches 2^64 (bc_out is then left unchanged),
+ * GBBC_ERR_INVALID for bad arguments, a CSR that fails the check, or
  * pointers in the wrong memory, GBBC_ERR_CUDA.
  */
 #define GBBC_NOALLOC_MAX_VERTICES 16384

@@ -98,11 +98,51 @@ struct gbbc_graph {
     };
     std::vector<Worker> workers;
     cudaEvent_t ev_start = nullptr;
+    // persistent grid schedule: device copies of the slots, their control
+    // words and level boundaries, the launch's control block and wide list
+    Slot* p_slots = nullptr;
+    PCtl* p_ctl = nullptr;
+    long long* p_lev = nullptr;
+    int p_lev_rows = 0;
+    PGlobal* p_glob = nullptr;
+    int32_t* p_wide = nullptr;
+    long long p_wide_cap = 0;
+    int p_blocks = 0;                // cooperative grid (0: not yet asked)
+    bool p_dirty = false;            // a launch stopped early: heavy-row accumulators may hold partial sums
+    cudaEvent_t p_ev[2] = {nullptr, nullptr};  // around each persistent launch
     // kept per-source state of the last bc_compute
     int32_t* k_dist = nullptr;
     uint64_t* k_sigma = nullptr;
     uint8_t* k_ovf = nullptr;
     long long k_count = 0;
+    // partitioned method (bc_partition): the parts, the intra-part and the
+    // border-edge CSRs, the border nodes and their matrices, and the border
+    // arrays of one batch
+    struct Part {
+        int32_t P = 0;                  // parts (0: not partitioned)
+        int32_t* part = nullptr;        // [n] part of each vertex
+        int32_t* in_rp = nullptr;       // [n + 1] intra-part CSR (border edges removed)
+        int32_t* in_col = nullptr;
+        long long in_nnz = 0;
+        int32_t* cut_rp = nullptr;      // [n + 1] border edges only
+        int32_t* cut_col = nullptr;
+        long long cut_nnz = 0;
+        long long nbt = 0;              // border nodes
+        int32_t* border = nullptr;      // [nbt] vertex of each border node (by part, then id)
+        int32_t* bidx = nullptr;        // [n] border index of each vertex, or -1
+        int32_t* bpart = nullptr;       // [nbt] part of each border node
+        long long* boff = nullptr;      // [P + 1] first border index of each part
+        long long* moff = nullptr;      // [P + 1] first entry of each part's matrix block
+        std::vector<long long> h_boff, h_moff;
+        int32_t* BM = nullptr;          // border matrices: shortest distances inside the part
+        PartWide SM;                    // sigma matrices: shortest-path counts inside the part
+        int32_t* D = nullptr;           // [nbt][64] refined distances of a batch
+        int32_t* D1 = nullptr;          // [nbt][64] Step 1 distances
+        PartWide S1, A, Sig;            // [nbt][64] Step 1 sigma, arrivals, sigma
+        int* changed = nullptr;
+        int32_t* lane_b = nullptr;      // [64] border index of each lane's source
+        long long sweeps = 0;           // refinement sweeps of the last bc_compute_partitioned
+    } pt;
 };
 
 namespace {
@@ -795,6 +835,233 @@ gbbc_status alloc_keep(gbbc_graph* g, long long k, cudaStream_t st) {
     return GBBC_OK;
 }
 
+// ---- host-driven forward and backward of one batch over a given CSR -------
+// (the partitioned method runs its BFS steps on the intra-part graph and its
+// backward phase on the whole graph)
+
+// Called by run_forward after the discovery and after the gather of each new
+// level (the partitioned method injects its border seeds there).
+struct FwdHooks {
+    virtual gbbc_status after_discovery(int level, const Slot& s, bool wide, cudaStream_t st) = 0;
+    virtual gbbc_status after_gather(int level, const Slot& s, bool wide, cudaStream_t st) = 0;
+    virtual ~FwdHooks() {}
+};
+
+// Forward phase of batch b over CSR c on slot s: level l's entries end up in
+// [off[l], off[l + 1]).  *carry: a count reached 2^64 in the narrow format
+// (the pass stopped there; rerun wide).
+gbbc_status run_forward(gbbc_graph* g, const Csr& c, const BatchDesc& b, cudaStream_t st, bool wide, Slot& s,
+                        gbbc_stats& stats, std::vector<long long>& off, bool* carry, FwdHooks* hooks) {
+    *carry = false;
+    const int32_t lo = b.lo, hi = b.hi;
+    const size_t rn = (size_t)(hi - lo);
+    const int hd = g->opt.heavy_degree;
+    const int policy = effective_policy(g);
+    CK(g, cudaMemsetAsync(s.vis + lo, 0, rn * sizeof(u64), st));
+    CK(g, cudaMemsetAsync(s.nx + lo, 0, rn * sizeof(u64), st));
+    CK(g, cudaMemsetAsync(s.ovf + lo, 0, rn * sizeof(u64), st));
+    CK(g, cudaMemsetAsync(s.F + lo, 0xff, rn * sizeof(MaskTag), st));
+    CK(g, cudaMemsetAsync(s.F + s.n + lo, 0xff, rn * sizeof(MaskTag), st));
+    CK(g, cudaMemcpyAsync(s.d_src, b.src, b.nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    std::vector<int32_t> distinct(b.src, b.src + b.nsrc);
+    std::sort(distinct.begin(), distinct.end());
+    distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
+    const long long nq0 = (long long)distinct.size();
+    std::memset(s.hctr, 0, sizeof(Counters));
+    s.hctr->qtail = (unsigned long long)nq0;
+    s.hctr->lane_sum = (unsigned long long)b.nsrc;
+    s.hctr->lanes = (b.nsrc == 64) ? ~0ull : ((1ull << b.nsrc) - 1ull);
+    CK(g, cudaMemcpyAsync(s.ctr, s.hctr, sizeof(Counters), cudaMemcpyHostToDevice, st));
+    launch_seed(s, b.nsrc, st);
+    const long long n_range = hi - lo;
+    const long long nnz_range = (long long)g->h_row_ptr[hi] - g->h_row_ptr[lo];
+    const long long max_deg = g->graph_max_deg[b.gi];
+    launch_decide(s, 0, 0, policy, g->d_policy, n_range, nnz_range, max_deg, st);
+    stats.kernel_launches += 2;
+    CK(g, cudaGetLastError());
+    CK(g, cudaMemcpyAsync(s.hctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(g, cudaStreamSynchronize(st));
+    off.assign({0, nq0});
+    u64 lanes = s.hctr->lanes;
+    int level = 0;
+    const size_t disc_off = offsetof(Counters, heavy), disc_bytes = offsetof(Counters, err) - disc_off;
+    const size_t gath_off = offsetof(Counters, lane_sum), gath_bytes = offsetof(Counters, medium) - gath_off;
+    for (;;) {
+        const long long q_lo = off[level], q_hi = off[level + 1];
+        const bool pull = s.hctr->dir != 0;
+        CK(g, cudaMemsetAsync((char*)s.ctr + disc_off, 0, disc_bytes, st));
+        if (pull) {
+            launch_pull(c, s, lo, hi, lanes, level, hd, g->nsm, st);
+            stats.levels_pull++;
+        } else {
+            launch_push(c, s, q_lo, q_hi, level, hd, g->nsm, st);
+            stats.levels_push++;
+        }
+        if (hooks) CKS(hooks->after_discovery(level + 1, s, wide, st));
+        CK(g, cudaMemsetAsync((char*)s.ctr + gath_off, 0, gath_bytes, st));
+        launch_fwd_gather(c, s, q_hi, level, hd, g->nsm, st, wide);
+        if (hooks) CKS(hooks->after_gather(level + 1, s, wide, st));
+        launch_decide(s, q_hi, level + 1, policy, g->d_policy, n_range, nnz_range, max_deg, st);
+        stats.kernel_launches += 7;
+        CK(g, cudaGetLastError());
+        CK(g, cudaMemcpyAsync(s.hctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        CK(g, cudaStreamSynchronize(st));
+        if (s.hctr->err)
+            return fail(g, GBBC_ERR_CAPACITY, "queue capacity exceeded in the forward phase (flags %u)", s.hctr->err);
+        const long long new_hi = (long long)s.hctr->qtail;
+        if (new_hi == q_hi) break;
+        if (s.hctr->carry && !wide) {
+            *carry = true;
+            break;
+        }
+        off.push_back(new_hi);
+        lanes = s.hctr->lanes;
+        ++level;
+    }
+    stats.levels_fwd += level + 1;
+    return GBBC_OK;
+}
+
+// Backward phase over CSR c for the levels of off (deepest first), BC into bc.
+gbbc_status run_backward(gbbc_graph* g, const Csr& c, Slot& s, const std::vector<long long>& off, bool wide, u64* bc,
+                         gbbc_stats& stats, cudaStream_t st) {
+    const int nlev = (int)off.size() - 1;
+    for (int l = nlev - 1; l >= 1; --l) {
+        CK(g, cudaMemsetAsync(&s.ctr->heavy, 0, 2 * sizeof(unsigned long long), st));  // heavy, tasks
+        launch_bwd(c, s, bc, off[l], off[l + 1], l, g->opt.heavy_degree, g->nsm, st, wide);
+        stats.kernel_launches += 3;
+    }
+    CK(g, cudaGetLastError());
+    return GBBC_OK;
+}
+
+// ---- the partitioned method (Sec. IV and Sec. V-A of the paper) -------------
+
+void free_partition(gbbc_graph* g) {
+    gbbc_graph::Part& q = g->pt;
+    for (void* p : {(void*)q.part, (void*)q.in_rp, (void*)q.in_col, (void*)q.cut_rp, (void*)q.cut_col,
+                    (void*)q.border, (void*)q.bidx, (void*)q.bpart, (void*)q.boff, (void*)q.moff, (void*)q.BM,
+                    (void*)q.SM.mod, (void*)q.SM.N, (void*)q.SM.X, (void*)q.SM.big, (void*)q.D, (void*)q.D1,
+                    (void*)q.S1.mod, (void*)q.S1.N, (void*)q.S1.X, (void*)q.S1.big, (void*)q.A.mod, (void*)q.A.N,
+                    (void*)q.A.X, (void*)q.A.big, (void*)q.Sig.mod, (void*)q.Sig.N, (void*)q.Sig.X,
+                    (void*)q.Sig.big, (void*)q.changed, (void*)q.lane_b})
+        dfree(g, p);
+    q = gbbc_graph::Part();
+}
+
+gbbc_status alloc_wide_arr(gbbc_graph* g, PartWide& w, size_t count) {
+    CKS(dalloc_t(g, &w.mod, count));
+    CKS(dalloc_t(g, &w.N, count));
+    CKS(dalloc_t(g, &w.X, count));
+    CKS(dalloc_t(g, &w.big, count));
+    return GBBC_OK;
+}
+
+gbbc_status clear_wide_arr(gbbc_graph* g, const PartWide& w, size_t count, cudaStream_t st) {
+    CK(g, cudaMemsetAsync(w.mod, 0, count * sizeof(u64), st));
+    CK(g, cudaMemsetAsync(w.big, 0, count, st));
+    return GBBC_OK;
+}
+
+// Forward of one batch over the intra-part graph, rerun wide when a count
+// reaches 2^64 (later batches of the handle then start wide).
+gbbc_status part_forward(gbbc_graph* g, const Csr& cin, const BatchDesc& b, cudaStream_t st, bool& wide,
+                         std::vector<long long>& off, FwdHooks* hooks) {
+    bool carry = false;
+    if (wide) CKS(alloc_wide(g, g->slot));
+    CKS(run_forward(g, cin, b, st, wide, g->slot, g->stats, off, &carry, hooks));
+    if (carry) {
+        CKS(alloc_wide(g, g->slot));
+        wide = true;
+        g->wide_graph[0] = 1;
+        g->stats.wide_batches++;
+        CKS(run_forward(g, cin, b, st, true, g->slot, g->stats, off, &carry, hooks));
+    }
+    return GBBC_OK;
+}
+
+// Step 6 seeds: inject the border nodes at their refined distances.
+struct SeedHooks : FwdHooks {
+    gbbc_graph* g;
+    explicit SeedHooks(gbbc_graph* h) : g(h) {}
+    gbbc_status after_discovery(int level, const Slot& s, bool wide, cudaStream_t st) override {
+        (void)wide;
+        launch_seed_inject(s, level, g->pt.border, g->pt.nbt, g->pt.D, g->pt.A, g->pt.in_rp, g->nsm, st);
+        g->stats.kernel_launches++;
+        return GBBC_OK;
+    }
+    gbbc_status after_gather(int level, const Slot& s, bool wide, cudaStream_t st) override {
+        launch_seed_add(s, level, g->pt.border, g->pt.nbt, g->pt.D, g->pt.A, wide, g->nsm, st);
+        g->stats.kernel_launches++;
+        return GBBC_OK;
+    }
+};
+
+// One batch by the partitioned method: Step 1, Steps 2-5, border sigma,
+// Step 6, kept state, backward over the whole graph.
+gbbc_status part_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
+    gbbc_graph::Part& q = g->pt;
+    Csr cin{g->n, q.in_nnz, q.in_rp, q.in_col};
+    Csr call{g->n, g->nnz, g->d_row_ptr, g->d_col};
+    const size_t cells = (size_t)std::max<long long>(q.nbt, 1) * kLanes;
+    bool wide = g->wide_graph[0] != 0;
+    std::vector<long long> off;
+    // Step 1: BFS inside each source's part; its border nodes' dist and sigma
+    CKS(part_forward(g, cin, b, st, wide, off, nullptr));
+    CK(g, cudaMemsetAsync(q.D1, 0x7f, cells * sizeof(int32_t), st));
+    CKS(clear_wide_arr(g, q.S1, cells, st));
+    CKS(clear_wide_arr(g, q.A, cells, st));
+    CKS(clear_wide_arr(g, q.Sig, cells, st));
+    for (size_t l = 0; l + 1 < off.size(); ++l)
+        launch_part_extract(g->slot, off[l], off[l + 1], (int)l, wide, 1, q.bidx, q.bpart, q.boff, q.moff, nullptr,
+                            q.D1, q.S1.mod, q.S1.N, q.S1.X, q.S1.big, g->nsm, st);
+    CK(g, cudaMemcpyAsync(q.D, q.D1, cells * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    // Steps 2-5: sweeps over the border edges and the border matrices until
+    // no border distance changes
+    long long sweeps = 0;
+    for (;;) {
+        int changed = 0;
+        CK(g, cudaMemsetAsync(q.changed, 0, sizeof(int), st));
+        launch_refine_cut(q.cut_rp, q.cut_col, q.border, q.bidx, q.nbt, q.D, q.changed, g->nsm, st);
+        launch_refine_bm(q.bpart, q.boff, q.moff, q.BM, q.nbt, q.D, q.changed, g->nsm, st);
+        g->stats.kernel_launches += 2;
+        CK(g, cudaMemcpyAsync(&changed, q.changed, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(g, cudaStreamSynchronize(st));
+        ++sweeps;
+        if (!changed) break;
+        if (sweeps > q.nbt + 2) return fail(g, GBBC_ERR_CAPACITY, "partitioned method: refinement did not settle");
+    }
+    q.sweeps += sweeps;
+    // sigma of the border nodes, level by level
+    std::vector<int32_t> hD(cells);
+    CK(g, cudaMemcpyAsync(hD.data(), q.D, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(g, cudaStreamSynchronize(st));
+    int32_t maxD = -1;
+    for (int32_t d : hD)
+        if (d < kPartInf) maxD = std::max(maxD, d);
+    for (int32_t l = 0; l <= maxD; ++l) {
+        launch_border_sigma_level(l, q.cut_rp, q.cut_col, q.border, q.bidx, q.bpart, q.boff, q.moff, q.BM, q.SM, q.nbt,
+                                  q.D, q.D1, q.S1, q.A, q.Sig, g->nsm, st);
+        g->stats.kernel_launches += 2;
+    }
+    // Step 6: relaxation inside every part, seeded at the border nodes
+    SeedHooks hooks(g);
+    CKS(part_forward(g, cin, b, st, wide, off, &hooks));
+    const int nlev = (int)off.size() - 1;
+    if (g->k_dist) {
+        for (int l = 0; l < nlev; ++l)
+            launch_keep_dist(g->slot, off[l], off[l + 1], l, g->k_dist, g->n, b.first, b.nsrc, st);
+        launch_keep_sigma(g->slot, b.lo, b.hi, g->k_sigma, g->k_ovf, g->n, b.first, b.nsrc, st);
+        g->stats.kernel_launches += nlev + 1;
+    }
+    // backward phase over the whole graph (successors across border edges too)
+    CKS(run_backward(g, call, g->slot, off, wide, g->d_bc, g->stats, st));
+    if (wide) g->stats.wide_batches++;
+    g->stats.batches++;
+    g->stats.sources += b.nsrc;
+    return GBBC_OK;
+}
+
 gbbc_status dispatch(gbbc_graph* g, const std::vector<BatchDesc>& bs, cudaStream_t st);
 gbbc_status grouping_scores(gbbc_graph* g, const std::vector<int32_t>& src, const std::vector<int32_t>& gid,
                             std::vector<float>& score, cudaStream_t st);
@@ -1356,7 +1623,26 @@ gbbc_status ensure_workers(gbbc_graph* g, int count) {
     return GBBC_OK;
 }
 
+gbbc_status run_persistent(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaStream_t st,
+                           std::vector<BatchDesc>& wide_out);
+gbbc_status run_grid_host(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaStream_t st);
+
+// The grid schedule: the persistent kernel for narrow batches, unless the
+// level loop must run on the host (tracing, kept state, GBBC_HOST_LOOP), in
+// which case (and for batches in the wide format) the host drives it.
 gbbc_status run_grid_batches(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaStream_t st) {
+    if (nb == 0) return GBBC_OK;
+    const bool host_loop = (g->opt.flags & (GBBC_TRACE | GBBC_HOST_LOOP)) || g->k_dist;
+    if (host_loop) return run_grid_host(g, bs, nb, st);
+    std::vector<BatchDesc> narrow, wide;
+    for (size_t i = 0; i < nb; ++i) (g->wide_graph[bs[i].gi] ? wide : narrow).push_back(bs[i]);
+    CKS(run_persistent(g, narrow.data(), narrow.size(), st, wide));
+    return run_grid_host(g, wide.data(), wide.size(), st);
+}
+
+// The grid schedule driven from the host: per-step kernels and a counter
+// read-back per level, up to opt.streams batches at once on host threads.
+gbbc_status run_grid_host(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaStream_t st) {
     if (nb == 0) return GBBC_OK;
     CKS(alloc_slot(g));
     const int C = grid_workers(g, nb);
@@ -1401,6 +1687,138 @@ gbbc_status run_grid_batches(gbbc_graph* g, const BatchDesc* bs, size_t nb, cuda
     }
     CK(g, cudaGetLastError());
     return (gbbc_status)status.load();
+}
+
+// The persistent grid schedule (bc_persist.cu): every narrow batch of the
+// call in one cooperative launch, W batches in flight on W slots (the handle's
+// slot and the workers' slots), the level loop on the device.  Batches whose
+// counts reach 2^64 come back in a list and are rerun wide by the host loop.
+#ifndef GBBC_DEFAULT_SPINS
+#define GBBC_DEFAULT_SPINS 100000000LL
+#endif
+gbbc_status run_persistent(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaStream_t st,
+                           std::vector<BatchDesc>& wide_out) {
+    if (nb == 0) return GBBC_OK;
+    CKS(alloc_slot(g));
+    const int W = std::max(1, std::min(grid_workers(g, nb), kMaxPSlots));
+    CKS(ensure_workers(g, W - 1));
+    if (g->p_blocks == 0) {
+        const int per_sm = persist_blocks_per_sm();
+        if (per_sm < 1) return fail(g, GBBC_ERR_CUDA, "persistent kernel: occupancy query failed");
+        g->p_blocks = per_sm * g->nsm;
+    }
+    const size_t n2 = (size_t)std::max<int32_t>(g->n, 1) + 2;
+    if (!g->p_slots) {
+        CKS(dalloc_t(g, &g->p_slots, kMaxPSlots));
+        CKS(dalloc_t(g, &g->p_ctl, kMaxPSlots));
+        CKS(dalloc_t(g, &g->p_glob, 1));
+    }
+    if (g->p_lev_rows < W) {
+        dfree(g, g->p_lev);
+        g->p_lev = nullptr;
+        CKS(dalloc_t(g, &g->p_lev, (size_t)W * n2));
+        g->p_lev_rows = W;
+    }
+    if (g->p_wide_cap < (long long)nb) {
+        dfree(g, g->p_wide);
+        g->p_wide = nullptr;
+        CKS(dalloc_t(g, &g->p_wide, nb));
+        g->p_wide_cap = (long long)nb;
+    }
+    std::vector<Slot> hs((size_t)W);
+    hs[0] = g->slot;
+    for (int w = 1; w < W; ++w) hs[w] = g->workers[w - 1].slot;
+    if (g->p_dirty) {  // an earlier launch stopped in the middle of a step
+        for (const Slot& x : hs) {
+            CK(g, cudaMemsetAsync(x.hacc, 0, (size_t)x.hcap * kLanes * 2 * sizeof(u64), st));
+            CK(g, cudaMemsetAsync(x.hcarry, 0, (size_t)x.hcap * sizeof(u64), st));
+        }
+        g->p_dirty = false;
+    }
+    std::vector<BlockBatch> hb(nb);
+    std::vector<int32_t> hsrc;
+    for (size_t i = 0; i < nb; ++i) {
+        hb[i].gi = bs[i].gi;
+        hb[i].lo = bs[i].lo;
+        hb[i].hi = bs[i].hi;
+        hb[i].nsrc = bs[i].nsrc;
+        hb[i].src_off = (long long)hsrc.size();
+        hb[i].wide = 0;
+        hb[i].pad = 0;
+        hsrc.insert(hsrc.end(), bs[i].src, bs[i].src + bs[i].nsrc);
+    }
+    if (g->d_bb_cap < (long long)nb) {
+        dfree(g, g->d_bb);
+        CKS(dalloc_t(g, &g->d_bb, nb));
+        g->d_bb_cap = (long long)nb;
+    }
+    if (g->d_bsrc_cap < (long long)hsrc.size()) {
+        dfree(g, g->d_bsrc);
+        CKS(dalloc_t(g, &g->d_bsrc, hsrc.size()));
+        g->d_bsrc_cap = (long long)hsrc.size();
+    }
+    CKS(ensure_graph_arrays(g));
+    for (const Slot& x : hs) CK(g, cudaMemsetAsync(x.ctr, 0, sizeof(Counters), st));
+    CK(g, cudaMemcpyAsync(g->p_slots, hs.data(), W * sizeof(Slot), cudaMemcpyHostToDevice, st));
+    CK(g, cudaMemsetAsync(g->p_ctl, 0, W * sizeof(PCtl), st));
+    CK(g, cudaMemsetAsync(g->p_glob, 0, sizeof(PGlobal), st));
+    CK(g, cudaMemcpyAsync(g->d_bb, hb.data(), nb * sizeof(BlockBatch), cudaMemcpyHostToDevice, st));
+    CK(g, cudaMemcpyAsync(g->d_bsrc, hsrc.data(), hsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    const long long spins = g->opt.timeout_spins > 0 ? (long long)g->opt.timeout_spins : GBBC_DEFAULT_SPINS;
+    Csr c{g->n, g->nnz, g->d_row_ptr, g->d_col};
+    if (!g->p_ev[0]) {
+        CK(g, cudaEventCreate(&g->p_ev[0]));
+        CK(g, cudaEventCreate(&g->p_ev[1]));
+    }
+    CK(g, cudaEventRecord(g->p_ev[0], st));
+    CK(g, launch_persist(c, g->p_slots, W, g->p_ctl, g->p_lev, (long long)n2, g->d_bb, (int)nb, g->d_bsrc, g->d_bc,
+                         effective_policy(g), g->d_policy, g->d_graph_max_deg, g->opt.heavy_degree, spins, g->p_glob,
+                         g->p_wide, g->p_blocks, st));
+    CK(g, cudaEventRecord(g->p_ev[1], st));
+    g->stats.kernel_launches++;
+    PGlobal hg;
+    CK(g, cudaMemcpyAsync(&hg, g->p_glob, sizeof(PGlobal), cudaMemcpyDeviceToHost, st));
+    CK(g, cudaStreamSynchronize(st));
+    {
+        float ms = 0.f;
+        CK(g, cudaEventElapsedTime(&ms, g->p_ev[0], g->p_ev[1]));
+        g->stats.persist_launches++;
+        g->stats.persist_ms += ms;
+        g->stats.persist_slots = W;
+        g->stats.persist_blocks = g->p_blocks;
+    }
+    if (hg.err & 1u) {
+        g->p_dirty = true;
+        return fail(g, GBBC_ERR_TIMEOUT,
+                    "persistent grid schedule: a grid barrier wait passed timeout_spins=%lld polls; the handle's BC "
+                    "is undefined until bc_reset", spins);
+    }
+    if (hg.err & 2u) {
+        g->p_dirty = true;
+        return fail(g, GBBC_ERR_CAPACITY,
+                    "persistent grid schedule: capacity exceeded (flags %u, step kind %u, direction %u, level %u)",
+                    hg.err_info & 15u, (hg.err_info >> 4) & 7u, (hg.err_info >> 7) & 1u, (hg.err_info >> 8) & 0xffffu);
+    }
+    std::vector<int32_t> wl(hg.wide);
+    if (hg.wide)
+        CK(g, cudaMemcpy(wl.data(), g->p_wide, hg.wide * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<char> rerun(nb, 0);
+    for (int32_t b : wl)
+        if (b >= 0 && (size_t)b < nb) rerun[b] = 1;
+    g->stats.batches += (long long)hg.batches;
+    g->stats.levels_fwd += (long long)hg.levels_fwd;
+    g->stats.levels_pull += (long long)hg.levels_pull;
+    g->stats.levels_push += (long long)(hg.levels_fwd - hg.levels_pull);
+    for (size_t i = 0; i < nb; ++i) {
+        if (rerun[i]) {
+            std::lock_guard<std::recursive_mutex> lk(g->mtx);
+            g->wide_graph[bs[i].gi] = 1;  // later batches of this graph start wide
+            wide_out.push_back(bs[i]);
+        } else {
+            g->stats.sources += bs[i].nsrc;
+        }
+    }
+    return GBBC_OK;
 }
 
 double now_s() {
@@ -1775,6 +2193,38 @@ gbbc_status bc_read_fixed(gbbc_graph* g, uint64_t* out, int32_t graph_id, void* 
     return GBBC_OK;
 }
 
+gbbc_status bc_add_fixed(gbbc_graph* g, const uint64_t* partial, int32_t graph_id, void* stream) {
+    if (!g) return GBBC_ERR_INVALID;
+    if (!partial) return fail(g, GBBC_ERR_INVALID, "partial is NULL");
+    int32_t count = (int32_t)g->goff.size() - 1;
+    if (graph_id < -1 || graph_id >= count) return fail(g, GBBC_ERR_INVALID, "graph_id %d", graph_id);
+    long long lo = graph_id < 0 ? 0 : g->goff[graph_id];
+    long long hi = graph_id < 0 ? g->n : g->goff[graph_id + 1];
+    cudaStream_t st = (cudaStream_t)stream;
+    if (hi > lo) {
+        const size_t bytes = (size_t)(hi - lo) * 2 * sizeof(u64);
+        const u64* src = reinterpret_cast<const u64*>(partial);
+        u64* stage = nullptr;
+        if (!is_device_ptr(partial)) {  // host partial: stage it on the device
+            CKS(dalloc(g, (void**)&stage, bytes));
+            cudaError_t e = cudaMemcpyAsync(stage, partial, bytes, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) {
+                dfree(g, stage);
+                return fail(g, GBBC_ERR_CUDA, "staging copy failed: %s", cudaGetErrorString(e));
+            }
+            src = stage;
+        }
+        launch_add_fixed(g->d_bc + 2 * lo, src, hi - lo, st);
+        g->stats.kernel_launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (stage) dfree(g, stage);
+        if (e != cudaSuccess) return fail(g, GBBC_ERR_CUDA, "bc_add_fixed: %s", cudaGetErrorString(e));
+    }
+    g->last_stream = st;
+    return GBBC_OK;
+}
+
 gbbc_status bc_read_source_state(gbbc_graph* g, int64_t source_index, int32_t* dist, uint64_t* sigma,
                                  uint8_t* overflow) {
     if (!g) return GBBC_ERR_INVALID;
@@ -1824,6 +2274,8 @@ void bc_graph_destroy(gbbc_graph* g) {
         if (w.ev) cudaEventDestroy(w.ev);
     }
     if (g->ev_start) cudaEventDestroy(g->ev_start);
+    for (cudaEvent_t e : g->p_ev)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
     delete g;
 }
@@ -1968,6 +2420,181 @@ gbbc_status bc_get_profile(const gbbc_graph* g, gbbc_kernel_profile* out, int32_
     if (!g || (max > 0 && !out)) return GBBC_ERR_INVALID;
     if (count) *count = PK_COUNT;
     for (int k = 0; k < PK_COUNT && k < max; ++k) out[k] = g->prof[k];
+    return GBBC_OK;
+}
+
+gbbc_status bc_partition(gbbc_graph* g, const int32_t* part, int32_t P, void* stream) {
+    if (!g) return GBBC_ERR_INVALID;
+    if (g->goff.size() != 2 || g->d_w)
+        return fail(g, GBBC_ERR_INVALID, "bc_partition: single-graph, unweighted handles only");
+    if (P < 1 || P > std::max<int32_t>(g->n, 1)) return fail(g, GBBC_ERR_INVALID, "bc_partition: P = %d", P);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t n = g->n;
+    std::vector<int32_t> hp;
+    if (part) {
+        CKS(to_host(g, hp, part, (size_t)n, st));
+        for (int32_t v = 0; v < n; ++v)
+            if (hp[v] < 0 || hp[v] >= P) return fail(g, GBBC_ERR_INVALID, "part[%d] = %d outside [0, %d)", v, hp[v], P);
+    } else {  // P contiguous ranges of vertex ids
+        hp.resize((size_t)n);
+        for (int32_t v = 0; v < n; ++v) hp[v] = (int32_t)(((long long)v * P) / std::max<int32_t>(n, 1));
+    }
+    std::vector<int32_t> col((size_t)g->nnz);
+    if (g->nnz > 0)
+        CK(g, cudaMemcpy(col.data(), g->d_col, (size_t)g->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    // intra-part and border-edge CSRs, border nodes by part then id
+    const std::vector<int32_t>& rp = g->h_row_ptr;
+    std::vector<int32_t> in_rp((size_t)n + 1, 0), cut_rp((size_t)n + 1, 0), in_col, cut_col;
+    in_col.reserve((size_t)g->nnz);
+    for (int32_t v = 0; v < n; ++v) {
+        for (int32_t p = rp[v]; p < rp[v + 1]; ++p) (hp[col[p]] == hp[v] ? in_col : cut_col).push_back(col[p]);
+        in_rp[v + 1] = (int32_t)in_col.size();
+        cut_rp[v + 1] = (int32_t)cut_col.size();
+    }
+    std::vector<std::vector<int32_t>> byp((size_t)P);
+    for (int32_t v = 0; v < n; ++v)
+        if (cut_rp[v + 1] > cut_rp[v]) byp[hp[v]].push_back(v);
+    std::vector<int32_t> border, bpart, bidx((size_t)n, -1);
+    std::vector<long long> boff((size_t)P + 1, 0), moff((size_t)P + 1, 0);
+    for (int32_t q = 0; q < P; ++q) {
+        for (int32_t v : byp[q]) {
+            bidx[v] = (int32_t)border.size();
+            border.push_back(v);
+            bpart.push_back(q);
+        }
+        const long long B = (long long)byp[q].size();
+        boff[q + 1] = boff[q] + B;
+        moff[q + 1] = moff[q] + B * B;
+    }
+    const long long nbt = (long long)border.size(), entries = moff[P];
+    const double need = (double)entries * (4 + 21) + (double)nbt * kLanes * (2 * 4 + 3 * 21);
+    if (entries >= 0x7fffffffLL || need > 0.5 * (double)avail_bytes(g->device))
+        return fail(g, GBBC_ERR_OOM, "bc_partition: %lld border nodes need %.3g bytes of border matrices", nbt, need);
+    free_partition(g);
+    gbbc_graph::Part& q = g->pt;
+    const size_t n1 = (size_t)std::max<int32_t>(n, 1);
+    const size_t e1 = (size_t)std::max<long long>(entries, 1), c1 = (size_t)std::max<long long>(nbt, 1) * kLanes;
+    CKS(dalloc_t(g, &q.part, n1));
+    CKS(dalloc_t(g, &q.in_rp, n1 + 1));
+    CKS(dalloc_t(g, &q.in_col, std::max<size_t>(in_col.size(), 1)));
+    CKS(dalloc_t(g, &q.cut_rp, n1 + 1));
+    CKS(dalloc_t(g, &q.cut_col, std::max<size_t>(cut_col.size(), 1)));
+    CKS(dalloc_t(g, &q.border, std::max<size_t>(border.size(), 1)));
+    CKS(dalloc_t(g, &q.bidx, n1));
+    CKS(dalloc_t(g, &q.bpart, std::max<size_t>(bpart.size(), 1)));
+    CKS(dalloc_t(g, &q.boff, boff.size()));
+    CKS(dalloc_t(g, &q.moff, moff.size()));
+    CKS(dalloc_t(g, &q.BM, e1));
+    CKS(alloc_wide_arr(g, q.SM, e1));
+    CKS(dalloc_t(g, &q.D, c1));
+    CKS(dalloc_t(g, &q.D1, c1));
+    CKS(alloc_wide_arr(g, q.S1, c1));
+    CKS(alloc_wide_arr(g, q.A, c1));
+    CKS(alloc_wide_arr(g, q.Sig, c1));
+    CKS(dalloc_t(g, &q.changed, 1));
+    CKS(dalloc_t(g, &q.lane_b, kLanes));
+    q.in_nnz = (long long)in_col.size();
+    q.cut_nnz = (long long)cut_col.size();
+    q.nbt = nbt;
+    q.h_boff = boff;
+    q.h_moff = moff;
+    CKS(to_device(g, q.part, hp.data(), (size_t)n * sizeof(int32_t), st));
+    CKS(to_device(g, q.in_rp, in_rp.data(), in_rp.size() * sizeof(int32_t), st));
+    CKS(to_device(g, q.in_col, in_col.data(), in_col.size() * sizeof(int32_t), st));
+    CKS(to_device(g, q.cut_rp, cut_rp.data(), cut_rp.size() * sizeof(int32_t), st));
+    CKS(to_device(g, q.cut_col, cut_col.data(), cut_col.size() * sizeof(int32_t), st));
+    CKS(to_device(g, q.border, border.data(), border.size() * sizeof(int32_t), st));
+    CKS(to_device(g, q.bidx, bidx.data(), (size_t)n * sizeof(int32_t), st));
+    CKS(to_device(g, q.bpart, bpart.data(), bpart.size() * sizeof(int32_t), st));
+    CKS(to_device(g, q.boff, boff.data(), boff.size() * sizeof(long long), st));
+    CKS(to_device(g, q.moff, moff.data(), moff.size() * sizeof(long long), st));
+    launch_fill_i32(q.BM, (long long)e1, -1, st);
+    CKS(clear_wide_arr(g, q.SM, e1, st));
+    // border matrices (Sec. IV-B) and sigma matrices (Sec. V-A): a BFS inside
+    // its part from every border node, 64 border nodes per batch
+    CKS(alloc_slot(g));
+    Csr cin{n, q.in_nnz, q.in_rp, q.in_col};
+    bool wide = g->wide_graph[0] != 0;
+    for (long long b0 = 0; b0 < nbt; b0 += kLanes) {
+        BatchDesc bd;
+        bd.gi = 0;
+        bd.lo = 0;
+        bd.hi = n;
+        bd.first = 0;
+        bd.nsrc = (int)std::min<long long>(kLanes, nbt - b0);
+        int32_t lane_b[kLanes];
+        for (int j = 0; j < kLanes; ++j) lane_b[j] = j < bd.nsrc ? (int32_t)(b0 + j) : -1;
+        for (int j = 0; j < bd.nsrc; ++j) bd.src[j] = border[(size_t)(b0 + j)];
+        CK(g, cudaMemcpyAsync(q.lane_b, lane_b, sizeof(lane_b), cudaMemcpyHostToDevice, st));
+        std::vector<long long> off;
+        CKS(part_forward(g, cin, bd, st, wide, off, nullptr));
+        for (size_t l = 0; l + 1 < off.size(); ++l)
+            launch_part_extract(g->slot, off[l], off[l + 1], (int)l, wide, 0, q.bidx, q.bpart, q.boff, q.moff,
+                                q.lane_b, q.BM, q.SM.mod, q.SM.N, q.SM.X, q.SM.big, g->nsm, st);
+        CK(g, cudaGetLastError());
+        CK(g, cudaStreamSynchronize(st));  // lane_b is reused by the next batch
+    }
+    q.P = P;
+    g->last_stream = st;
+    return GBBC_OK;
+}
+
+gbbc_status bc_partition_info(const gbbc_graph* g, gbbc_partition_info* out) {
+    if (!g || !out) return GBBC_ERR_INVALID;
+    std::memset(out, 0, sizeof(*out));
+    out->parts = g->pt.P;
+    out->border_nodes = g->pt.nbt;
+    out->border_edges = g->pt.cut_nnz;
+    out->intra_entries = g->pt.in_nnz;
+    out->matrix_entries = g->pt.P ? g->pt.h_moff.back() : 0;
+    out->refinement_sweeps = g->pt.sweeps;
+    return GBBC_OK;
+}
+
+gbbc_status bc_read_border_matrix(gbbc_graph* g, int32_t p, int64_t* nodes, int32_t* border, int32_t* bm,
+                                  uint64_t* sigma_m, uint8_t* overflow) {
+    if (!g) return GBBC_ERR_INVALID;
+    const gbbc_graph::Part& q = g->pt;
+    if (!q.P) return fail(g, GBBC_ERR_STATE, "no partition (bc_partition)");
+    if (p < 0 || p >= q.P) return fail(g, GBBC_ERR_INVALID, "part %d outside [0, %d)", p, q.P);
+    const long long b0 = q.h_boff[p], B = q.h_boff[p + 1] - b0, m0 = q.h_moff[p];
+    if (nodes) *nodes = B;
+    CK(g, cudaStreamSynchronize(g->last_stream));
+    if (B == 0) return GBBC_OK;
+    if (border) CK(g, cudaMemcpy(border, q.border + b0, (size_t)B * sizeof(int32_t), cudaMemcpyDefault));
+    if (bm) CK(g, cudaMemcpy(bm, q.BM + m0, (size_t)(B * B) * sizeof(int32_t), cudaMemcpyDefault));
+    if (sigma_m) CK(g, cudaMemcpy(sigma_m, q.SM.mod + m0, (size_t)(B * B) * sizeof(uint64_t), cudaMemcpyDefault));
+    if (overflow) CK(g, cudaMemcpy(overflow, q.SM.big + m0, (size_t)(B * B), cudaMemcpyDefault));
+    return GBBC_OK;
+}
+
+gbbc_status bc_compute_partitioned(gbbc_graph* g, const int32_t* sources, int64_t k, void* stream) {
+    if (!g) return GBBC_ERR_INVALID;
+    if (!g->pt.P) return fail(g, GBBC_ERR_STATE, "no partition (call bc_partition first)");
+    if (k < 0 || (k > 0 && !sources)) return fail(g, GBBC_ERR_INVALID, "bad source list");
+    if (g->opt.batch_width == 1) return fail(g, GBBC_ERR_INVALID, "the partitioned method has no one-source form");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> src;
+    CKS(to_host(g, src, sources, (size_t)k, st));
+    for (long long i = 0; i < k; ++i)
+        if (src[i] < 0 || src[i] >= g->n)
+            return fail(g, GBBC_ERR_INVALID, "source %lld = %d outside [0, %d)", i, src[i], g->n);
+    CKS(alloc_keep(g, k, st));
+    CKS(alloc_slot(g));
+    g->last_stream = st;
+    g->pt.sweeps = 0;
+    const int width = g->opt.batch_width == 32 ? 32 : kLanes;
+    for (long long i = 0; i < k; i += width) {
+        BatchDesc b;
+        b.gi = 0;
+        b.lo = 0;
+        b.hi = g->n;
+        b.first = i;
+        b.nsrc = (int)std::min<long long>(width, k - i);
+        for (int j = 0; j < b.nsrc; ++j) b.src[j] = src[(size_t)(i + j)];
+        CKS(part_batch(g, b, st));
+    }
+    CK(g, cudaStreamSynchronize(st));
     return GBBC_OK;
 }
 

@@ -150,6 +150,86 @@ struct BlockSlots {
     Counters* ctr = nullptr;  // [slot]
 };
 
+// ---- persistent multi-batch kernel of the grid schedule (bc_persist.cu) ----
+// One cooperative launch runs every batch of a call: up to kMaxPSlots batches
+// are in flight at once, each on a batch slot of its own, and the level loop
+// runs on the device.  A "tick" is one level step of every batch in flight
+// (batch init, top-down or bottom-up discovery, sigma gather, or backward
+// step), in four phases separated by grid-wide barriers: rows (a warp per
+// item), heavy-row chunk tasks (a block per item), heavy-row finish (a warp
+// per item), and the bookkeeping of each batch (a warp per batch: direction
+// decision, level advance, next batch).
+constexpr int kMaxPSlots = 16;
+constexpr int kPBlock = 256;  // threads per block of the persistent kernel
+
+enum PPhase { PH_IDLE = 0, PH_INIT = 1, PH_DISC = 2, PH_GATHER = 3, PH_BWD = 4, PH_DONE = 5 };
+
+// State of one batch slot between ticks (device memory, written by the
+// slot's bookkeeping warp, read by every block after the barrier).
+struct __align__(16) PCtl {
+    int32_t phase;       // PPhase
+    int32_t batch;       // batch index
+    int32_t level;       // forward: level whose discovery / gather runs; backward: level
+    int32_t dir;         // direction of the discovery step (0 push, 1 pull)
+    int32_t lo, hi;      // vertex range of the batch's graph
+    int32_t nlev;        // forward levels of the batch (set when the forward ends)
+    int32_t npull;       // bottom-up steps of the batch
+    long long q_lo, q_hi;// entry range of the step (gather: new entries [q_hi, new_hi))
+    long long new_hi;    // end of the entries the discovery queued
+    long long items;     // warp items of the step's first phase
+    u64 lanes;           // active lanes (bottom-up steps)
+};
+
+// Whole-launch control: grid barrier, error bits, batch work list, stats.
+struct __align__(16) PGlobal {
+    unsigned bar_count;  // blocks arrived at the current barrier
+    unsigned bar_gen;    // barrier generation
+    unsigned err;        // bit 0: a barrier wait gave up; bit 1: queue capacity
+    unsigned next;       // next batch of the work list
+    unsigned long long batches, levels_fwd, levels_pull;
+    unsigned wide;       // batches whose counts reached 2^64 (listed in wide_list)
+    unsigned err_info;   // with err bit 1: the slot's error bits, step kind, direction and level
+};
+
+// Resident blocks of the persistent kernel per SM (0 if the query fails).
+int persist_blocks_per_sm();
+// Launch it cooperatively on `blocks` blocks (at most SMs x resident blocks).
+// slots: W device Slot structs; ctl: W PCtl (zeroed: idle); lev: W rows of
+// lev_stride level boundaries; bc: the handle's BC (exact atomic adds).
+cudaError_t launch_persist(const Csr& g, const Slot* slots, int W, PCtl* ctl, long long* lev, long long lev_stride,
+                           const BlockBatch* batches, int nb, const int32_t* srcs, u64* bc, int policy,
+                           const void* weights_fp16, const long long* graph_max_deg, int heavy_deg,
+                           long long spin_limit, PGlobal* G, int32_t* wide_list, int blocks, cudaStream_t st);
+
+// ---- the partitioned method (bc_partition.cu) ----
+constexpr int32_t kPartInf = 0x7f7f7f7f;  // an unreached border distance (memset 0x7f)
+// Path counts of border nodes (lane-minor, [border][64]) or of a border
+// matrix: value mod 2^64, a flag for values >= 2^64, and then an
+// approximation N * 2^X with a normalised 64-bit mantissa.
+struct PartWide {
+    u64* mod = nullptr;
+    u64* N = nullptr;
+    int32_t* X = nullptr;
+    uint8_t* big = nullptr;
+};
+void launch_part_extract(const Slot& s, long long q_lo, long long q_hi, int level, bool wide, int mode,
+                         const int32_t* bidx, const int32_t* bpart, const long long* boff, const long long* moff,
+                         const int32_t* lane_b, int32_t* dist_out, u64* mod, u64* N, int32_t* X, uint8_t* big,
+                         int nsm, cudaStream_t st);
+void launch_refine_cut(const int32_t* cut_rp, const int32_t* cut_col, const int32_t* border, const int32_t* bidx,
+                       long long nbt, int32_t* D, int* changed, int nsm, cudaStream_t st);
+void launch_refine_bm(const int32_t* bpart, const long long* boff, const long long* moff, const int32_t* BM,
+                      long long nbt, int32_t* D, int* changed, int nsm, cudaStream_t st);
+void launch_border_sigma_level(int level, const int32_t* cut_rp, const int32_t* cut_col, const int32_t* border,
+                               const int32_t* bidx, const int32_t* bpart, const long long* boff,
+                               const long long* moff, const int32_t* BM, const PartWide& SM, long long nbt,
+                               const int32_t* D, const int32_t* D1, const PartWide& S1, const PartWide& A,
+                               const PartWide& Sig, int nsm, cudaStream_t st);
+void launch_seed_inject(const Slot& s, int level, const int32_t* border, long long nbt, const int32_t* D,
+                        const PartWide& A, const int32_t* row_ptr, int nsm, cudaStream_t st);
+void launch_seed_add(const Slot& s, int level, const int32_t* border, long long nbt, const int32_t* D,
+                     const PartWide& A, bool wide, int nsm, cudaStream_t st);
+
 // ---- launch wrappers (bc_kernels.cu) ----
 void launch_seed(const Slot& s, int nsrc, cudaStream_t st);
 void launch_push(const Csr& g, const Slot& s, long long q_lo, long long q_hi, int level, int heavy_deg,

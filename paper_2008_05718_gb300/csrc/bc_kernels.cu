@@ -16,50 +16,9 @@
 #include "bc_fixed.cuh"
 #include "bc_internal.cuh"
 #include "bc_policy.cuh"
+#include "bc_rows.cuh"
 
 namespace gbbc {
-
-#define FULL 0xffffffffu
-
-__device__ __forceinline__ u64 warp_or64(u64 x) {
-    unsigned lo = __reduce_or_sync(FULL, (unsigned)x);
-    unsigned hi = __reduce_or_sync(FULL, (unsigned)(x >> 32));
-    return ((u64)hi << 32) | lo;
-}
-
-__device__ __forceinline__ u64 shfl64(u64 x, int src) {
-    return __shfl_sync(FULL, x, src);
-}
-
-// Append `item` for the threads with pred set, one atomic per warp.  All
-// 32 threads of the warp must call this.  Returns false on overflow.
-__device__ __forceinline__ void warp_append(bool pred, int32_t item, unsigned long long* counter, int32_t* list,
-                                            long long cap, unsigned* err, unsigned errbit) {
-    const int lane = threadIdx.x & 31;
-    unsigned bal = __ballot_sync(FULL, pred);
-    if (!bal) return;
-    int leader = __ffs(bal) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(bal));
-    base = __shfl_sync(FULL, base, leader);
-    if (pred) {
-        unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
-        if ((long long)pos < cap) list[pos] = item;
-        else atomicOr(err, errbit);
-    }
-}
-
-// Loads of slot data: NC = the data is read-only for the whole kernel (one
-// kernel per step), so the non-coherent path may serve it; the persistent
-// block kernel rewrites slot data between its own steps and uses L2-coherent
-// loads instead.
-template <bool NC>
-__device__ __forceinline__ u64 ldv(const u64* p) { return NC ? __ldg(p) : __ldcg(p); }
-template <bool NC>
-__device__ __forceinline__ int ldi(const int* p) { return NC ? __ldg(p) : __ldcg(p); }
-
-__device__ __forceinline__ long long gwarp() { return ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
-__device__ __forceinline__ long long nwarps() { return ((long long)gridDim.x * blockDim.x) >> 5; }
 
 static int grid_for(long long warps_needed, int nsm, int per_sm = 8) {
     long long blocks = (warps_needed * kWarp + kBlock - 1) / kBlock;
@@ -111,117 +70,10 @@ __global__ void k_seed(Slot s, int nsrc) {
 void launch_seed(const Slot& s, int nsrc, cudaStream_t st) { k_seed<<<1, kLanes, 0, st>>>(s, nsrc); }
 
 // ---------------------------------------------------------------------------
-// Heavy rows: a warp that meets entry e with more than heavy_deg neighbours
-// reserves an accumulator slot h and ceil(deg / kChunk) chunk tasks.  All 32
-// threads of the warp call this.
-__device__ __forceinline__ void enqueue_heavy(const Slot& s, long long e, int32_t beg, int32_t end) {
-    const int lane = threadIdx.x & 31;
-    const int nch = (end - beg + kChunk - 1) / kChunk;
-    unsigned long long h = 0, t0 = 0;
-    if (lane == 0) {
-        h = atomicAdd(&s.ctr->heavy, 1ull);
-        t0 = atomicAdd(&s.ctr->tasks, (unsigned long long)nch);
-    }
-    h = __shfl_sync(FULL, h, 0);
-    t0 = __shfl_sync(FULL, t0, 0);
-    if ((long long)h >= s.hcap || (long long)(t0 + nch) > s.tcap) {
-        if (lane == 0) atomicOr(&s.ctr->err, 2u);
-        return;
-    }
-    if (lane == 0) s.hentry[h] = (int32_t)e;
-    for (int i = lane; i < nch; i += 32) s.tasks[t0 + i] = make_int2((int)h, beg + i * kChunk);
-}
-
-// Task t of this step, validated against the capacities (a task slot that
-// an overflowing reservation left unwritten is skipped).
-__device__ __forceinline__ bool load_task(const Slot& s, const Csr& g, long long t, int& h, long long& e,
-                                          int32_t& v, u64& m, int32_t& p0, int32_t& p1) {
-    int2 tk = s.tasks[t];
-    h = tk.x;
-    if (h < 0 || h >= s.hcap) return false;
-    e = s.hentry[h];
-    if (e < 0 || e >= s.qcap) return false;
-    v = s.qv[e];
-    if (v < 0 || v >= g.n) return false;
-    m = s.qm[e];
-    int32_t beg = g.row_ptr[v], end = g.row_ptr[v + 1];
-    p0 = tk.y;
-    if (p0 < beg || p0 >= end) return false;
-    p1 = p0 + kChunk < end ? p0 + kChunk : end;
-    return true;
-}
-
-__device__ __forceinline__ long long task_count(const Slot& s) {
-    long long c = (long long)s.ctr->tasks;
-    return c < s.tcap ? c : s.tcap;
-}
-
-__device__ __forceinline__ long long heavy_count(const Slot& s) {
-    long long c = (long long)s.ctr->heavy;
-    return c < s.hcap ? c : s.hcap;
-}
-
-// ---------------------------------------------------------------------------
-// Top-down discovery: for each frontier entry (v, m) and neighbour w, the
-// lanes m & ~vis[w] reach w at the next level.  atomicOr collects them in
-// nx[w]; the thread that turns nx[w] from 0 to non-zero queues w.
-// Statistics of the next frontier gathered by the discovery kernels: the sum
-// of degrees of newly queued vertices and the OR of the lanes reaching them.
-struct StepStats {
-    unsigned long long esum;
-    unsigned long long scanned;
-    u64 lanes;
-};
-
-__device__ __forceinline__ void flush_stats(const Slot& s, StepStats st) {
-    // all 32 threads of the warp call this
-    unsigned long long e = st.esum, c = st.scanned;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        e += __shfl_xor_sync(FULL, e, o);
-        c += __shfl_xor_sync(FULL, c, o);
-    }
-    u64 l = warp_or64(st.lanes);
-    if ((threadIdx.x & 31) == 0 && (e | l | c)) {
-        atomicAdd(&s.ctr->edge_sum, e);
-        atomicAdd(&s.ctr->scanned, c);
-        atomicOr(&s.ctr->lanes, l);
-    }
-}
-
-__device__ __forceinline__ void push_row(const Csr& g, const Slot& s, u64 m, int32_t beg, int32_t end, int t,
-                                         int nthreads, StepStats& stats) {
-    for (int32_t base = beg; base < end; base += nthreads) {
-        int32_t p = base + t;
-        bool newq = false;
-        int32_t w = 0;
-        if (p < end) {
-            w = __ldg(g.col + p);
-            u64 nm = m & ~s.vis[w];
-            if (nm) {
-                u64 old = atomicOr(&s.nx[w], nm);
-                newq = (old == 0);
-                stats.lanes |= nm;
-                if (newq) stats.esum += (unsigned long long)(__ldg(g.row_ptr + w + 1) - __ldg(g.row_ptr + w));
-            }
-        }
-        warp_append(newq, w, &s.ctr->qtail, s.qv, s.qcap, &s.ctr->err, 1u);
-    }
-}
-
+// Top-down discovery: a warp per frontier entry (push_entry).
 __global__ void k_push(Csr g, Slot s, long long q_lo, long long q_hi, int heavy_deg) {
-    const int lane = threadIdx.x & 31;
     StepStats stats = {0ull, 0ull, 0ull};
-    for (long long e = q_lo + gwarp(); e < q_hi; e += nwarps()) {
-        int32_t v = s.qv[e];
-        u64 m = s.qm[e];
-        int32_t beg = __ldg(g.row_ptr + v), end = __ldg(g.row_ptr + v + 1);
-        if (end - beg > heavy_deg) {
-            enqueue_heavy(s, e, beg, end);
-            continue;
-        }
-        push_row(g, s, m, beg, end, lane, kWarp, stats);
-    }
+    for (long long e = q_lo + gwarp(); e < q_hi; e += nwarps()) push_entry(g, s, e, heavy_deg, stats);
     flush_stats(s, stats);
 }
 
@@ -229,14 +81,7 @@ __global__ void k_push(Csr g, Slot s, long long q_lo, long long q_hi, int heavy_
 __global__ void k_push_tasks(Csr g, Slot s) {
     const long long cnt = task_count(s);
     StepStats stats = {0ull, 0ull, 0ull};
-    for (long long t = blockIdx.x; t < cnt; t += gridDim.x) {
-        int h;
-        long long e;
-        int32_t v, p0, p1;
-        u64 m;
-        if (!load_task(s, g, t, h, e, v, m, p0, p1)) continue;
-        push_row(g, s, m, p0, p1, threadIdx.x, blockDim.x, stats);
-    }
+    for (long long t = blockIdx.x; t < cnt; t += gridDim.x) push_task(g, s, t, stats);
     flush_stats(s, stats);
 }
 
@@ -250,381 +95,56 @@ void launch_push(const Csr& g, const Slot& s, long long q_lo, long long q_hi, in
 }
 
 // ---------------------------------------------------------------------------
-// Bottom-up discovery over the vertex range [lo, hi): w collects the OR of
-// its neighbours' level-`level` frontier masks, restricted to the lanes that
-// still miss w; the scan stops once every such lane is found.
-// Rows up to 32 entries: one thread per row.  Longer rows go to a list that
-// k_pull_medium (a warp per row) or k_pull_heavy (a block per row) handles.
-__global__ void k_pull_thread(Csr g, Slot s, int32_t lo, int32_t hi, u64 lanes, int level, int heavy_deg,
-                              int32_t* medium, unsigned long long* n_medium) {
-    const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+// Bottom-up discovery over the vertex range [lo, hi): a warp per 32
+// consecutive vertices (pull_vertices); rows longer than 32 entries are
+// deferred to k_pull_medium (a warp per row) or k_pull_heavy (a block per
+// row).
+__global__ void k_pull_thread(Csr g, Slot s, int32_t lo, int32_t hi, u64 lanes, int level, int heavy_deg) {
     StepStats stats = {0ull, 0ull, 0ull};
-    for (long long base = (long long)lo + (long long)blockIdx.x * blockDim.x; base < hi; base += stride) {
-        int32_t w = (int32_t)(base + threadIdx.x);
-        u64 u = 0;
-        int32_t beg = 0, end = 0;
-        bool defer_med = false, defer_heavy = false;
-        if (w < hi) {
-            u = ~s.vis[w] & lanes;
-            if (u) {
-                beg = __ldg(g.row_ptr + w);
-                end = __ldg(g.row_ptr + w + 1);
-                if (end - beg > heavy_deg) { defer_heavy = true; u = 0; }
-                else if (end - beg > kWarp) { defer_med = true; u = 0; }
-            }
-        }
-        u64 f = 0;
-        if (u) {
-            for (int32_t p = beg; p < end; ++p) {
-                ++stats.scanned;
-                int32_t v = __ldg(g.col + p);
-                MaskTag t = F[v];
-                if (t.tag == level) {
-                    f |= t.mask;
-                    if ((f & u) == u) break;
-                }
-            }
-        }
-        u64 nm = f & u;
-        if (nm) {
-            s.nx[w] = nm;
-            stats.lanes |= nm;
-            stats.esum += (unsigned long long)(end - beg);
-        }
-        warp_append(nm != 0, w, &s.ctr->qtail, s.qv, s.qcap, &s.ctr->err, 1u);
-        warp_append(defer_med, w, n_medium, medium, s.n, &s.ctr->err, 2u);
-        warp_append(defer_heavy, w, &s.ctr->heavy, s.heavy, s.n, &s.ctr->err, 2u);
-    }
+    for (long long base = (long long)lo + gwarp() * kWarp; base < hi; base += nwarps() * kWarp)
+        pull_vertices(g, s, base, hi, lanes, level, heavy_deg, stats);
     flush_stats(s, stats);
 }
 
-// Warp per row (medium rows).
-__global__ void k_pull_medium(Csr g, Slot s, u64 lanes, int level, const int32_t* medium,
-                              const unsigned long long* n_medium) {
-    const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
-    const int lane = threadIdx.x & 31;
-    const long long cnt = (long long)*n_medium;
+__global__ void k_pull_medium(Csr g, Slot s, u64 lanes, int level) {
+    const long long cnt = (long long)s.ctr->medium;
     StepStats stats = {0ull, 0ull, 0ull};
-    for (long long i = gwarp(); i < cnt; i += nwarps()) {
-        int32_t w = medium[i];
-        u64 u = ~s.vis[w] & lanes;
-        int32_t beg = g.row_ptr[w], end = g.row_ptr[w + 1];
-        u64 f = 0;
-        for (int32_t base = beg; base < end; base += kWarp) {
-            int32_t p = base + lane;
-            if (p < end) {
-                ++stats.scanned;
-                MaskTag t = F[__ldg(g.col + p)];
-                if (t.tag == level) f |= t.mask;
-            }
-            f = warp_or64(f);
-            if ((f & u) == u) break;
-        }
-        u64 nm = f & u;
-        if (nm && lane == 0) {
-            s.nx[w] = nm;
-            stats.lanes |= nm;
-            stats.esum += (unsigned long long)(end - beg);
-        }
-        warp_append(nm != 0 && lane == 0, w, &s.ctr->qtail, s.qv, s.qcap, &s.ctr->err, 1u);
-    }
+    for (long long i = gwarp(); i < cnt; i += nwarps()) pull_medium_row(g, s, lanes, level, s.medium[i], stats);
     flush_stats(s, stats);
 }
 
-// Block per row (heavy rows).  No early exit: a block-wide OR per row.
 __global__ void k_pull_heavy(Csr g, Slot s, u64 lanes, int level) {
-    const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
     __shared__ u64 part[kHeavyBlock / kWarp];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const long long cnt = (long long)s.ctr->heavy;
     StepStats stats = {0ull, 0ull, 0ull};
-    for (long long h = blockIdx.x; h < cnt; h += gridDim.x) {
-        int32_t w = s.heavy[h];
-        u64 u = ~s.vis[w] & lanes;
-        int32_t beg = g.row_ptr[w], end = g.row_ptr[w + 1];
-        u64 f = 0;
-        for (int32_t p = beg + threadIdx.x; p < end; p += blockDim.x) {
-            ++stats.scanned;
-            MaskTag t = F[__ldg(g.col + p)];
-            if (t.tag == level) f |= t.mask;
-        }
-        f = warp_or64(f);
-        if (lane == 0) part[wid] = f;
-        __syncthreads();
-        if (wid == 0) {
-            u64 x = lane < nw ? part[lane] : 0;
-            x = warp_or64(x);
-            u64 nm = x & u;
-            if (nm && lane == 0) {
-                s.nx[w] = nm;
-                stats.lanes |= nm;
-                stats.esum += (unsigned long long)(end - beg);
-            }
-            warp_append(nm != 0 && lane == 0, w, &s.ctr->qtail, s.qv, s.qcap, &s.ctr->err, 1u);
-        }
-        __syncthreads();
-    }
+    for (long long h = blockIdx.x; h < cnt; h += gridDim.x) pull_heavy_row(g, s, lanes, level, s.heavy[h], part, stats);
     flush_stats(s, stats);
 }
 
 void launch_pull(const Csr& g, const Slot& s, int32_t lo, int32_t hi, u64 lanes, int level, int heavy_deg, int nsm,
                  cudaStream_t st) {
     if (hi <= lo) return;
-    int32_t* medium = s.medium;
-    unsigned long long* n_medium = &s.ctr->medium;
     long long range = (long long)hi - lo;
     long long blocks = (range + kBlock - 1) / kBlock;
     if (blocks > (long long)nsm * 8) blocks = (long long)nsm * 8;
-    k_pull_thread<<<(int)blocks, kBlock, 0, st>>>(g, s, lo, hi, lanes, level, heavy_deg, medium, n_medium);
-    k_pull_medium<<<nsm * 8, kBlock, 0, st>>>(g, s, lanes, level, medium, n_medium);
+    k_pull_thread<<<(int)blocks, kBlock, 0, st>>>(g, s, lo, hi, lanes, level, heavy_deg);
+    k_pull_medium<<<nsm * 8, kBlock, 0, st>>>(g, s, lanes, level);
     k_pull_heavy<<<nsm * 2, kHeavyBlock, 0, st>>>(g, s, lanes, level);
 }
 
 // ---------------------------------------------------------------------------
-// Forward gather + finalize for the entries queued at level `level`+1.
-// Finalize: the entry's mask is nx[w] (then cleared), vis[w] gains it, and
-// the dense frontier word of parity (level+1) is set.  Gather: for each lane
-// j of the mask, sigma[w][j] = sum over neighbours v whose level-`level`
-// mask has bit j of sigma[v][j], in CSR order, mod 2^64; a carry marks the
-// lane in ovf[w].  Thread t owns lanes t and t+32.
-//
-// WIDE additionally keeps sigma of overflowed lanes as N * 2^X (N a
-// normalised 64-bit mantissa, X an int32 exponent): terms are aligned to the
-// largest exponent seen and summed in a u128, so the mantissa keeps 64 bits.
-struct WideAcc {
-    u128 a;   // sum, units of 2^x
-    int x;    // exponent of a's unit; INT_MIN while empty
-    bool ovf; // a predecessor overflowed
-};
-
-__device__ __forceinline__ u128 shr128(u128 a, int r) {
-    u128 t;
-    if (r <= 0) return a;
-    if (r >= 128) { t.lo = t.hi = 0ull; return t; }
-    if (r >= 64) { t.lo = a.hi >> (r - 64); t.hi = 0ull; return t; }
-    t.lo = (a.lo >> r) | (a.hi << (64 - r));
-    t.hi = a.hi >> r;
-    return t;
-}
-
-__device__ __forceinline__ void wide_add(WideAcc& w, u128 v, int x) {
-    if (v.lo == 0ull && v.hi == 0ull) return;
-    if (w.x == INT_MIN) { w.a = v; w.x = x; return; }
-    if (x > w.x) { w.a = shr128(w.a, x - w.x); w.x = x; }
-    else v = shr128(v, w.x - x);
-    w.a = add128(w.a, v);
-}
-
-struct GatherAcc {
-    u64 a0, a1;
-    unsigned c0, c1;
-    WideAcc w0, w1;
-};
-
-__device__ __forceinline__ void gather_init(GatherAcc& acc) {
-    acc.a0 = acc.a1 = 0ull;
-    acc.c0 = acc.c1 = 0u;
-    acc.w0.a.lo = acc.w0.a.hi = acc.w1.a.lo = acc.w1.a.hi = 0ull;
-    acc.w0.x = acc.w1.x = INT_MIN;
-    acc.w0.ovf = acc.w1.ovf = false;
-}
-
-// sigma of predecessor (v, lane) as mantissa/exponent
-template <bool WIDE>
-__device__ __forceinline__ void pred_term(const Slot& s, int32_t v, int lane_id, u64 x, u64 ovf_v, WideAcc& w) {
-    if (!WIDE) return;
-    u128 t;
-    int X;
-    if ((ovf_v >> lane_id) & 1ull) {
-        t.lo = s.sN[(size_t)v * kLanes + lane_id];
-        X = s.sX[(size_t)v * kLanes + lane_id];
-        w.ovf = true;
-    } else {
-        t.lo = x;  // exact: x * 2^0
-        X = 0;
-    }
-    t.hi = 0ull;
-    wide_add(w, t, X);
-}
-
-// Up to four contributing neighbours per round: their (vertex, mask) pairs
-// are broadcast from the ballot, then all loads are issued before any is
-// used, so a warp keeps several independent loads in flight.
-#ifndef GBBC_GATHER_ROUND
-#define GBBC_GATHER_ROUND 4
-#endif
-// Occupancy hints for tuning builds only: an explicit minimum of blocks per
-// SM changes ptxas's register allocation, and the defaults (none for the
-// gather, the block size alone for the backward) measured fastest.
-#ifdef GBBC_GATHER_MIN_BLOCKS
-#define GBBC_GATHER_BOUNDS __launch_bounds__(kBlock, GBBC_GATHER_MIN_BLOCKS)
-#else
-#define GBBC_GATHER_BOUNDS
-#endif
-#ifdef GBBC_BWD_MIN_BLOCKS
-#define GBBC_BWD_BOUNDS __launch_bounds__(kBlock, GBBC_BWD_MIN_BLOCKS)
-#else
-#define GBBC_BWD_BOUNDS __launch_bounds__(kBlock)
-#endif
-
-template <int R>
-struct RoundR {
-    int32_t v[R];
-    u64 f[R];
-};
-typedef RoundR<4> Round4;
-
-template <int R>
-__device__ __forceinline__ void take_round(unsigned& bal, int32_t v, u64 f, RoundR<R>& r) {
-#pragma unroll
-    for (int u = 0; u < R; ++u) {
-        int src = bal ? __ffs(bal) - 1 : -1;
-        if (bal) bal &= bal - 1;
-        int sl = src < 0 ? 0 : src;
-        r.v[u] = __shfl_sync(FULL, v, sl);
-        u64 ff = shfl64(f, sl);
-        r.f[u] = src < 0 ? 0ull : ff;
-    }
-}
-
-template <int NT, bool WIDE, bool NC = true>
-__device__ __forceinline__ void fwd_gather_row(const Csr& g, const Slot& s, const MaskTag* F, int level, u64 m,
-                                               int32_t beg, int32_t end, int first, GatherAcc& acc) {
-    // this warp handles chunks starting at beg + first*32, stepping NT*32
-    const int lane = threadIdx.x & 31;
-    for (int32_t base = beg + first * kWarp; base < end; base += NT * kWarp) {
-        int32_t p = base + lane;
-        int32_t v = 0;
-        u64 f = 0;
-        if (p < end) {
-            v = __ldg(g.col + p);
-            MaskTag t = F[v];
-            if (t.tag == level) f = t.mask & m;
-        }
-        unsigned bal = __ballot_sync(FULL, f != 0);
-        if (WIDE) {
-            while (bal) {
-                int src = __ffs(bal) - 1;
-                bal &= bal - 1;
-                int32_t vv = __shfl_sync(FULL, v, src);
-                u64 ff = shfl64(f, src);
-                const u64* row = s.sigma + (size_t)vv * kLanes;
-                u64 ov = s.ovf[vv];
-                if ((ff >> lane) & 1ull) {
-                    u64 x = ldv<NC>(row + lane);
-                    acc.a0 += x;
-                    acc.c0 |= acc.a0 < x;
-                    pred_term<WIDE>(s, vv, lane, x, ov, acc.w0);
-                }
-                if ((ff >> (lane + 32)) & 1ull) {
-                    u64 x = ldv<NC>(row + lane + 32);
-                    acc.a1 += x;
-                    acc.c1 |= acc.a1 < x;
-                    pred_term<WIDE>(s, vv, lane + 32, x, ov, acc.w1);
-                }
-            }
-        } else {
-            while (bal) {
-                constexpr int R = GBBC_GATHER_ROUND;
-                RoundR<R> r;
-                take_round<R>(bal, v, f, r);
-                u64 x0[R], x1[R];
-#pragma unroll
-                for (int u = 0; u < R; ++u) {
-                    const u64* row = s.sigma + (size_t)r.v[u] * kLanes;
-                    x0[u] = ((r.f[u] >> lane) & 1ull) ? ldv<NC>(row + lane) : 0ull;
-                    x1[u] = ((r.f[u] >> (lane + 32)) & 1ull) ? ldv<NC>(row + lane + 32) : 0ull;
-                }
-#pragma unroll
-                for (int u = 0; u < R; ++u) {
-                    acc.a0 += x0[u];
-                    acc.c0 |= acc.a0 < x0[u];
-                    acc.a1 += x1[u];
-                    acc.c1 |= acc.a1 < x1[u];
-                }
-            }
-        }
-    }
-}
-
-template <bool WIDE>
-__device__ __forceinline__ void wide_store(const Slot& s, int32_t w, int lane_id, const WideAcc& a) {
-    // normalise to a 64-bit mantissa (truncating) and exponent
-    int lz = clz128(a.a);
-    int bits = 128 - lz;
-    u64 N;
-    if (bits > 64) N = shr128(a.a, bits - 64).lo;
-    else N = a.a.lo << (64 - bits);
-    s.sN[(size_t)w * kLanes + lane_id] = N;
-    s.sX[(size_t)w * kLanes + lane_id] = a.x + bits - 64;
-}
-
-template <bool WIDE>
-__device__ __forceinline__ void fwd_store(const Slot& s, int32_t w, u64 m, const GatherAcc& acc) {
-    const int lane = threadIdx.x & 31;
-    u64* row = s.sigma + (size_t)w * kLanes;
-    const bool l0 = (m >> lane) & 1ull, l1 = (m >> (lane + 32)) & 1ull;
-    if (l0) row[lane] = acc.a0;
-    if (l1) row[lane + 32] = acc.a1;
-    bool o0 = l0 && (acc.c0 || (WIDE && acc.w0.ovf));
-    bool o1 = l1 && (acc.c1 || (WIDE && acc.w1.ovf));
-    if (WIDE) {
-        if (o0) wide_store<WIDE>(s, w, lane, acc.w0);
-        if (o1) wide_store<WIDE>(s, w, lane + 32, acc.w1);
-    }
-    unsigned b0 = __ballot_sync(FULL, o0);
-    unsigned b1 = __ballot_sync(FULL, o1);
-    if (lane == 0 && (b0 | b1)) {
-        s.ovf[w] |= ((u64)b1 << 32) | b0;
-        atomicOr(&s.ctr->carry, 1u);
-    }
-}
-
+// Forward gather + finalize for the entries queued at level `level`+1
+// (gather_entry): thread t of a warp owns lanes t and t+32; the WIDE form
+// also keeps sigma of lanes past 2^64 as a mantissa and an exponent.
 template <bool WIDE>
 __global__ void GBBC_GATHER_BOUNDS k_fwd_gather(Csr g, Slot s, long long q_lo, int level, int heavy_deg) {
-    const int lane = threadIdx.x & 31;
     const long long q_hi = (long long)s.ctr->qtail;  // end of the entries the discovery queued
     const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
     MaskTag* Fn = s.F + (size_t)((level + 1) & 1) * s.n;
     unsigned long long lsum = 0, lesum = 0;
-    for (long long e = q_lo + gwarp(); e < q_hi; e += nwarps()) {
-        int32_t w = s.qv[e];
-        u64 m = s.nx[w];
-        int32_t beg = __ldg(g.row_ptr + w), end = __ldg(g.row_ptr + w + 1);
-        __syncwarp();
-        if (lane == 0) {
-            s.qm[e] = m;
-            s.nx[w] = 0;
-            s.vis[w] |= m;
-            MaskTag t;
-            t.mask = m;
-            t.tag = level + 1;
-            t.pad = 0;
-            Fn[w] = t;
-            unsigned pc = (unsigned)__popcll(m);
-            lsum += pc;
-            lesum += (unsigned long long)pc * (unsigned long long)(end - beg);
-        }
-        if (end - beg > heavy_deg) {
-            if (WIDE) {  // block per row (the wide sum is not order-free)
-                if (lane == 0) {
-                    unsigned long long pos = atomicAdd(&s.ctr->heavy, 1ull);
-                    if ((long long)pos < s.n) s.heavy[pos] = (int32_t)e;
-                    else atomicOr(&s.ctr->err, 2u);
-                }
-            } else {
-                __syncwarp();
-                enqueue_heavy(s, e, beg, end);
-            }
-            continue;
-        }
-        GatherAcc acc;
-        gather_init(acc);
-        fwd_gather_row<1, WIDE>(g, s, F, level, m, beg, end, 0, acc);
-        fwd_store<WIDE>(s, w, m, acc);
-    }
-    if (lane == 0 && lsum) {
+    for (long long e = q_lo + gwarp(); e < q_hi; e += nwarps())
+        gather_entry<WIDE, true>(g, s, F, Fn, level, e, heavy_deg, lsum, lesum);
+    if ((threadIdx.x & 31) == 0 && lsum) {
         atomicAdd(&s.ctr->lane_sum, lsum);
         atomicAdd(&s.ctr->lane_esum, lesum);
     }
@@ -674,77 +194,20 @@ __global__ void k_fwd_gather_heavy_wide(Csr g, Slot s, int level) {
     }
 }
 
-// Narrow format: chunk tasks of heavy rows (block of 8 warps per task) add
-// their per-lane partial sums into hacc[h][lane] with 64-bit atomics; a
-// carry of any add (or inside a partial) marks the lane in hcarry[h].
+// Narrow format: chunk tasks of heavy rows (block of 8 warps per task).
 __global__ void k_fwd_gather_tasks(Csr g, Slot s, int level) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int NW = kChunkBlock / kWarp;
     const MaskTag* F = s.F + (size_t)(level & 1) * s.n;
     __shared__ u64 ps[NW][kLanes];
     __shared__ unsigned pc[NW][kLanes];
     const long long cnt = task_count(s);
-    for (long long t = blockIdx.x; t < cnt; t += gridDim.x) {
-        int h;
-        long long e;
-        int32_t v, p0, p1;
-        u64 m;
-        bool ok = load_task(s, g, t, h, e, v, m, p0, p1);
-        GatherAcc acc;
-        gather_init(acc);
-        if (ok) fwd_gather_row<NW, false>(g, s, F, level, m, p0, p1, wid, acc);
-        ps[wid][lane] = acc.a0;
-        ps[wid][lane + 32] = acc.a1;
-        pc[wid][lane] = acc.c0;
-        pc[wid][lane + 32] = acc.c1;
-        __syncthreads();
-        if (wid == 0 && ok) {
-            u64 carry = 0;
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                int j = lane + 32 * half;
-                u64 sum = 0;
-                unsigned c = 0;
-                for (int i = 0; i < NW; ++i) {
-                    u64 x = ps[i][j];
-                    sum += x;
-                    c |= (sum < x) | pc[i][j];
-                }
-                if ((m >> j) & 1ull) {
-                    u64 old = atomicAdd(s.hacc + ((size_t)h * kLanes + j) * 2, sum);
-                    c |= (old + sum) < old;
-                    if (c) carry |= 1ull << j;
-                }
-            }
-            u64 cw = warp_or64(carry);
-            if (lane == 0 && cw) atomicOr(s.hcarry + h, cw);
-        }
-        __syncthreads();
-    }
+    for (long long t = blockIdx.x; t < cnt; t += gridDim.x) gather_task<NW, true>(g, s, F, level, t, ps, pc);
 }
 
 // Finish the heavy rows: warp per row reads and clears its accumulators.
 __global__ void k_fwd_gather_finish(Slot s) {
-    const int lane = threadIdx.x & 31;
     const long long cnt = heavy_count(s);
-    for (long long h = gwarp(); h < cnt; h += nwarps()) {
-        long long e = s.hentry[h];
-        int32_t w = s.qv[e];
-        u64 m = s.qm[e];
-        u64* a = s.hacc + (size_t)h * kLanes * 2;
-        GatherAcc acc;
-        gather_init(acc);
-        u64 cw = s.hcarry[h];
-        acc.a0 = a[2 * lane];
-        acc.a1 = a[2 * (lane + 32)];
-        acc.c0 = (unsigned)((cw >> lane) & 1ull);
-        acc.c1 = (unsigned)((cw >> (lane + 32)) & 1ull);
-        a[2 * lane] = 0ull;
-        a[2 * (lane + 32)] = 0ull;
-        __syncwarp();
-        if (lane == 0) s.hcarry[h] = 0ull;
-        fwd_store<false>(s, w, m, acc);
-    }
+    for (long long h = gwarp(); h < cnt; h += nwarps()) gather_finish(s, h);
 }
 
 void launch_fwd_gather(const Csr& g, const Slot& s, long long q_lo, int level, int heavy_deg, int nsm,
@@ -762,238 +225,29 @@ void launch_fwd_gather(const Csr& g, const Slot& s, long long q_lo, int level, i
 
 // ---------------------------------------------------------------------------
 // Backward step for the entries of level `level` (>= 1), in the integer
-// fixed-point form of bc_fixed.cuh.  Successors of (v, lane j) are the
-// neighbours w whose level-(level+1) mask has bit j.  Per (v, j):
+// fixed-point form of bc_fixed.cuh (bwd_entry).  Successors of (v, lane j)
+// are the neighbours w whose level-(level+1) mask has bit j.  Per (v, j):
 //   A     = sum over successors of psi_w * 2^(E_v + 64)       (u128)
 //   delta = N_v * A / 2^63                                    (units 2^-64)
 //   psi_v = (floor(2^127 / N_v) + A) * 2^(-64 - E_v)         (stored rounded)
 //   BC[v] += sum over lanes of delta                          (u128)
 // The entry's own mask is published with tag `level` for the next step.
-
-// sigma of (v, lane) as normalised mantissa N and exponent E = floor(log2)
-template <bool WIDE>
-__device__ __forceinline__ void sigma_norm(const Slot& s, int32_t v, int lane_id, u64 ovf_v, u64& N, int& E) {
-    if (WIDE && ((ovf_v >> lane_id) & 1ull)) {
-        N = s.sN[(size_t)v * kLanes + lane_id];
-        E = s.sX[(size_t)v * kLanes + lane_id] + 63;
-    } else {
-        u64 x = s.sigma[(size_t)v * kLanes + lane_id];
-        int lz = __clzll(x);
-        N = x << lz;
-        E = 63 - lz;
-    }
-}
-
-template <bool WIDE>
-__device__ __forceinline__ u128 psi_term(u64 bits, int eoff, int Ev) {
-    int e = (int)((bits >> 52) & 0x7FFull) - 1023 + (WIDE ? eoff : 0);
-    u64 M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    return shl_term(M, e + Ev + 12);
-}
-
-// Lane-compacted accumulation.  A round of up to four contributing
-// successors (slot u = 0..3, lanes f_u) is expanded into a list of
-// (slot, lane) terms, and each thread of the warp takes one term: it loads
-// psi[w_u][lane], shifts it to the lane's fixed point and adds it into
-// acc[u][lane] in shared memory.  Lanes are distinct within a slot, so the
-// adds need no atomics; the four slots are summed when the row is done.
-struct BwdWarpSmem {
-    u64 acc[4][kLanes][2];
-    int E[kLanes];
-    unsigned char list[4 * kLanes];
-};
-
-template <int NT, bool WIDE, bool NC = true>
-__device__ __forceinline__ void bwd_gather_row(const Csr& g, const Slot& s, const MaskTag* Fs, int level, u64 m,
-                                               int32_t beg, int32_t end, int first, BwdWarpSmem& sm) {
-    const int lane = threadIdx.x & 31;
-    const unsigned below = (1u << lane) - 1u;
-    for (int32_t base = beg + first * kWarp; base < end; base += NT * kWarp) {
-        int32_t p = base + lane;
-        int32_t w = 0;
-        u64 f = 0;
-        if (p < end) {
-            w = __ldg(g.col + p);
-            MaskTag t = Fs[w];
-            if (t.tag == level + 1) f = t.mask & m;
-        }
-        unsigned bal = __ballot_sync(FULL, f != 0);
-        while (bal) {
-            Round4 r;
-            take_round<4>(bal, w, f, r);
-            int K = 0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                unsigned lo = (unsigned)r.f[u], hi = (unsigned)(r.f[u] >> 32);
-                int clo = __popc(lo);
-                if ((lo >> lane) & 1u) sm.list[K + __popc(lo & below)] = (unsigned char)((u << 6) | lane);
-                if ((hi >> lane) & 1u) sm.list[K + clo + __popc(hi & below)] = (unsigned char)((u << 6) | (lane + 32));
-                K += clo + __popc(hi);
-            }
-            __syncwarp();
-            for (int i = lane; i < K; i += kWarp) {
-                unsigned code = sm.list[i];
-                int u = (int)(code >> 6), j = (int)(code & 63u);
-                int32_t wv = u == 0 ? r.v[0] : (u == 1 ? r.v[1] : (u == 2 ? r.v[2] : r.v[3]));
-                size_t at = (size_t)wv * kLanes + j;
-                u64 bits = ldv<NC>(s.psi + at);
-                int xo = WIDE ? ldi<NC>(s.psi_e + at) : 0;
-                u128 t = psi_term<WIDE>(bits, xo, sm.E[j]);
-                u64* a = sm.acc[u][j];
-                u128 cur = {a[0], a[1]};
-                cur = add128(cur, t);
-                a[0] = cur.lo;
-                a[1] = cur.hi;
-            }
-            __syncwarp();
-        }
-    }
-}
-
-// Before a row: publish the lanes' exponents.  After it: the lanes' sums
-// (slots added) for this thread's two lanes, leaving the slots at zero.
-__device__ __forceinline__ void bwd_row_begin(BwdWarpSmem& sm, int E0, int E1) {
-    const int lane = threadIdx.x & 31;
-    sm.E[lane] = E0;
-    sm.E[lane + 32] = E1;
-    __syncwarp();
-}
-
-__device__ __forceinline__ void bwd_row_end(BwdWarpSmem& sm, u128& a0, u128& a1) {
-    const int lane = threadIdx.x & 31;
-    __syncwarp();
-    a0.lo = a0.hi = a1.lo = a1.hi = 0ull;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        u128 x = {sm.acc[u][lane][0], sm.acc[u][lane][1]};
-        u128 y = {sm.acc[u][lane + 32][0], sm.acc[u][lane + 32][1]};
-        a0 = add128(a0, x);
-        a1 = add128(a1, y);
-        sm.acc[u][lane][0] = sm.acc[u][lane][1] = 0ull;
-        sm.acc[u][lane + 32][0] = sm.acc[u][lane + 32][1] = 0ull;
-    }
-    __syncwarp();
-}
-
-__device__ __forceinline__ void bwd_smem_zero(BwdWarpSmem& sm) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        sm.acc[u][lane][0] = sm.acc[u][lane][1] = 0ull;
-        sm.acc[u][lane + 32][0] = sm.acc[u][lane + 32][1] = 0ull;
-    }
-    __syncwarp();
-}
-
-// per-lane finish: delta (returned, units 2^-64) and psi_v (stored)
-template <bool WIDE>
-__device__ __forceinline__ u128 bwd_lane(const Slot& s, int32_t v, int lane_id, u64 N, int E, u128 A) {
-    u128 d = mul_shift63(N, A);
-    u128 psi = add128(recip127(N), A);
-    u64 M;
-    int e;
-    round128(psi, -64 - E, M, e);
-    size_t at = (size_t)v * kLanes + lane_id;
-    if (WIDE) {
-        s.psi[at] = unit_bits(M);
-        s.psi_e[at] = e;
-    } else {
-        s.psi[at] = double_bits(M, e);
-    }
-    return d;
-}
-
-__device__ __forceinline__ u128 shfl_xor128(u128 a, int o) {
-    u128 r;
-    r.lo = __shfl_xor_sync(FULL, a.lo, o);
-    r.hi = __shfl_xor_sync(FULL, a.hi, o);
-    return r;
-}
-
-__device__ __forceinline__ void atomic_add128(u64* a, u128 t);
-
-template <bool WIDE, bool ATOMIC_BC = false>
-__device__ __forceinline__ void bwd_store(const Slot& s, u64* bc, int32_t v, u64 m, int E0, int E1, u64 N0, u64 N1,
-                                          u128 a0, u128 a1) {
-    const int lane = threadIdx.x & 31;
-    u128 c;
-    c.lo = c.hi = 0ull;
-    if ((m >> lane) & 1ull) c = add128(c, bwd_lane<WIDE>(s, v, lane, N0, E0, a0));
-    if ((m >> (lane + 32)) & 1ull) c = add128(c, bwd_lane<WIDE>(s, v, lane + 32, N1, E1, a1));
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) c = add128(c, shfl_xor128(c, o));
-    if (lane == 0) {
-        if (ATOMIC_BC) {  // several batches of one graph may run at once
-            atomic_add128(bc + 2 * (size_t)v, c);
-        } else {
-            u128 b;
-            b.lo = bc[2 * (size_t)v];
-            b.hi = bc[2 * (size_t)v + 1];
-            b = add128(b, c);
-            bc[2 * (size_t)v] = b.lo;
-            bc[2 * (size_t)v + 1] = b.hi;
-        }
-    }
-}
-
-template <bool WIDE>
-__device__ __forceinline__ void lane_norms(const Slot& s, int32_t v, u64 m, u64& N0, int& E0, u64& N1, int& E1) {
-    const int lane = threadIdx.x & 31;
-    u64 ov = WIDE ? s.ovf[v] : 0ull;
-    N0 = N1 = 1ull << 63;
-    E0 = E1 = 0;
-    if ((m >> lane) & 1ull) sigma_norm<WIDE>(s, v, lane, ov, N0, E0);
-    if ((m >> (lane + 32)) & 1ull) sigma_norm<WIDE>(s, v, lane + 32, ov, N1, E1);
-}
-
 template <bool WIDE>
 __global__ void GBBC_BWD_BOUNDS k_bwd(Csr g, Slot s, u64* bc, long long q_lo, long long q_hi, int level,
-                                               int heavy_deg) {
-    const int lane = threadIdx.x & 31;
+                                     int heavy_deg) {
     __shared__ BwdWarpSmem smem[kBlock / kWarp];
     BwdWarpSmem& sm = smem[threadIdx.x >> 5];
     bwd_smem_zero(sm);
     const MaskTag* Fs = s.F + (size_t)((level + 1) & 1) * s.n;
     MaskTag* Fo = s.F + (size_t)(level & 1) * s.n;
-    for (long long e = q_lo + gwarp(); e < q_hi; e += nwarps()) {
-        int32_t v = s.qv[e];
-        u64 m = s.qm[e];
-        int32_t beg = __ldg(g.row_ptr + v), end = __ldg(g.row_ptr + v + 1);
-        if (lane == 0) {
-            MaskTag t;
-            t.mask = m;
-            t.tag = level;
-            t.pad = 0;
-            Fo[v] = t;
-        }
-        if (end - beg > heavy_deg) {
-            enqueue_heavy(s, e, beg, end);
-            continue;
-        }
-        u64 N0, N1;
-        int E0, E1;
-        lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
-        u128 a0, a1;
-        bwd_row_begin(sm, E0, E1);
-        bwd_gather_row<1, WIDE>(g, s, Fs, level, m, beg, end, 0, sm);
-        bwd_row_end(sm, a0, a1);
-        bwd_store<WIDE>(s, bc, v, m, E0, E1, N0, N1, a0, a1);
-    }
+    for (long long e = q_lo + gwarp(); e < q_hi; e += nwarps())
+        bwd_entry<WIDE, true, false>(g, s, bc, Fs, Fo, level, e, heavy_deg, sm);
 }
 
-// Chunk tasks of heavy rows: per-lane u128 partial sums are added into
-// hacc[h][lane] with two 64-bit atomics (the low word's carry goes into the
-// high word), which keeps the total exact whatever the order.
-__device__ __forceinline__ void atomic_add128(u64* a, u128 t) {
-    if ((t.lo | t.hi) == 0ull) return;
-    u64 old = atomicAdd(a, t.lo);
-    u64 carry = (old + t.lo) < old ? 1ull : 0ull;
-    if (t.hi + carry) atomicAdd(a + 1, t.hi + carry);
-}
-
+// Chunk tasks of heavy rows: per-lane u128 partial sums into hacc[h][lane].
 template <bool WIDE>
 __global__ void k_bwd_tasks(Csr g, Slot s, int level) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int wid = threadIdx.x >> 5;
     constexpr int NW = kChunkBlock / kWarp;
     const MaskTag* Fs = s.F + (size_t)((level + 1) & 1) * s.n;
     __shared__ u128 ps[NW][kLanes];
@@ -1001,56 +255,13 @@ __global__ void k_bwd_tasks(Csr g, Slot s, int level) {
     BwdWarpSmem& sm = smem[wid];
     bwd_smem_zero(sm);
     const long long cnt = task_count(s);
-    for (long long t = blockIdx.x; t < cnt; t += gridDim.x) {
-        int h;
-        long long e;
-        int32_t v, p0, p1;
-        u64 m;
-        bool ok = load_task(s, g, t, h, e, v, m, p0, p1);
-        u128 a0 = {0ull, 0ull}, a1 = {0ull, 0ull};
-        if (ok) {
-            u64 N0, N1;
-            int E0, E1;
-            lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
-            bwd_row_begin(sm, E0, E1);
-            bwd_gather_row<NW, WIDE>(g, s, Fs, level, m, p0, p1, wid, sm);
-            bwd_row_end(sm, a0, a1);
-        }
-        ps[wid][lane] = a0;
-        ps[wid][lane + 32] = a1;
-        __syncthreads();
-        if (wid == 0 && ok) {
-            u128 t0 = {0ull, 0ull}, t1 = {0ull, 0ull};
-            for (int i = 0; i < NW; ++i) {
-                t0 = add128(t0, ps[i][lane]);
-                t1 = add128(t1, ps[i][lane + 32]);
-            }
-            u64* a = s.hacc + (size_t)h * kLanes * 2;
-            atomic_add128(a + 2 * lane, t0);
-            atomic_add128(a + 2 * (lane + 32), t1);
-        }
-        __syncthreads();
-    }
+    for (long long t = blockIdx.x; t < cnt; t += gridDim.x) bwd_task<NW, WIDE, true>(g, s, Fs, level, t, sm, ps);
 }
 
 template <bool WIDE>
 __global__ void k_bwd_finish(Slot s, u64* bc) {
-    const int lane = threadIdx.x & 31;
     const long long cnt = heavy_count(s);
-    for (long long h = gwarp(); h < cnt; h += nwarps()) {
-        long long e = s.hentry[h];
-        int32_t v = s.qv[e];
-        u64 m = s.qm[e];
-        u64* a = s.hacc + (size_t)h * kLanes * 2;
-        u128 a0 = {a[2 * lane], a[2 * lane + 1]};
-        u128 a1 = {a[2 * (lane + 32)], a[2 * (lane + 32) + 1]};
-        a[2 * lane] = a[2 * lane + 1] = 0ull;
-        a[2 * (lane + 32)] = a[2 * (lane + 32) + 1] = 0ull;
-        u64 N0, N1;
-        int E0, E1;
-        lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
-        bwd_store<WIDE>(s, bc, v, m, E0, E1, N0, N1, a0, a1);
-    }
+    for (long long h = gwarp(); h < cnt; h += nwarps()) bwd_finish<WIDE, false>(s, bc, h);
 }
 
 void launch_bwd(const Csr& g, const Slot& s, u64* bc, long long q_lo, long long q_hi, int level, int heavy_deg,

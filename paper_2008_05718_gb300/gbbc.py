@@ -25,6 +25,7 @@ SCHEDULE = {"auto": 0, "grid": 1, "block": 2, "pair": 3}
 GBBC_KEEP_STATE = 1
 GBBC_TRACE = 2
 GBBC_TRACE_BOTH = 4
+GBBC_HOST_LOOP = 8
 
 # every symbol include/gbbc.h declares
 EXPORTS = ("bc_options_init", "bc_graph_create", "bc_graph_create_multi", "bc_graph_create_weighted", "bc_compute", "bc_compute_multi",
@@ -32,7 +33,8 @@ EXPORTS = ("bc_options_init", "bc_graph_create", "bc_graph_create_multi", "bc_gr
            "bc_last_error_detail", "bc_get_stats", "bc_get_trace", "bc_clear_trace", "bc_get_profile",
            "bc_compute_noalloc", "bc_mlp_param_count", "bc_mlp_forward", "bc_mlp_loss_grad", "bc_mlp_adam_step",
            "bc_mlp_train", "bc_policy_eval", "bc_policy_load", "bc_read_fixed", "bc_source_features",
-           "bc_grouping_load", "bc_grouping_scores", "bc_release_memory")
+           "bc_grouping_load", "bc_grouping_scores", "bc_release_memory", "bc_add_fixed", "bc_partition",
+           "bc_partition_info", "bc_read_border_matrix", "bc_compute_partitioned")
 NOALLOC_MAX_VERTICES = 16384
 MAX_WEIGHT = 64  # GBBC_MAX_WEIGHT
 
@@ -49,7 +51,9 @@ class gbbc_stats(ctypes.Structure):
                 ("levels_push", ctypes.c_int64), ("levels_pull", ctypes.c_int64), ("wide_batches", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("batch_width", ctypes.c_int32), ("policy", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("block_slots", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("block_slots", ctypes.c_int32),
+                ("persist_launches", ctypes.c_int64), ("persist_ms", ctypes.c_double),
+                ("persist_slots", ctypes.c_int32), ("persist_blocks", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,6 +74,12 @@ class gbbc_level_trace(ctypes.Structure):
 class gbbc_kernel_profile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
+
+
+class gbbc_partition_info(ctypes.Structure):
+    _fields_ = [("parts", ctypes.c_int32), ("border_nodes", ctypes.c_int64), ("border_edges", ctypes.c_int64),
+                ("intra_entries", ctypes.c_int64), ("matrix_entries", ctypes.c_int64),
+                ("refinement_sweeps", ctypes.c_int64)]
 
 
 class GbbcError(RuntimeError):
@@ -100,6 +110,11 @@ def load():
             "bc_read": (ctypes.c_int, [vp, vp, i32, vp]),
             "bc_read_source_state": (ctypes.c_int, [vp, i64, vp, vp, vp]),
             "bc_read_fixed": (ctypes.c_int, [vp, vp, i32, vp]),
+            "bc_add_fixed": (ctypes.c_int, [vp, vp, i32, vp]),
+            "bc_partition": (ctypes.c_int, [vp, vp, i32, vp]),
+            "bc_partition_info": (ctypes.c_int, [vp, P(gbbc_partition_info)]),
+            "bc_read_border_matrix": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, vp]),
+            "bc_compute_partitioned": (ctypes.c_int, [vp, vp, i64, vp]),
             "bc_reset": (ctypes.c_int, [vp]),
             "bc_sync": (ctypes.c_int, [vp]),
             "bc_graph_destroy": (None, [vp]),
@@ -278,6 +293,62 @@ def bc_read_fixed(handle, n, graph_id=-1, stream=None):
     out = np.zeros((int(n), 2), np.uint64)
     _check(load().bc_read_fixed(handle, out.ctypes.data, int(graph_id), _stream(stream)), handle)
     return out
+
+
+def bc_read_fixed_into(handle, out, graph_id=-1, stream=None):
+    """bc_read_fixed into a caller buffer (numpy uint64 / torch int64 or
+    uint64 [n, 2] or [2n], host or CUDA)."""
+    p, keep = _ptr(out)
+    _check(load().bc_read_fixed(handle, p, int(graph_id), _stream(stream)), handle)
+    return out
+
+
+def bc_add_fixed(handle, partial, graph_id=-1, stream=None):
+    """Add an exact fixed-point BC vector ([n, 2] / [2n] uint64 or int64,
+    host numpy or torch host/CUDA) into the handle's accumulated BC."""
+    if hasattr(partial, "data_ptr"):
+        p, keep = _ptr(partial)
+    else:
+        p, keep = _ptr(np.ascontiguousarray(partial, dtype=np.uint64))
+    _check(load().bc_add_fixed(handle, p, int(graph_id), _stream(stream)), handle)
+
+
+def bc_partition(handle, part=None, P=2, stream=None):
+    """Split the handle's graph into P parts (part: int32[n] host/device, or
+    None for P contiguous ranges) and build its border matrices."""
+    if part is None:
+        _check(load().bc_partition(handle, None, int(P), _stream(stream)), handle)
+        return
+    pp, keep = _ptr(_as_i32(part))
+    _check(load().bc_partition(handle, pp, int(P), _stream(stream)), handle)
+
+
+def bc_partition_info(handle) -> dict:
+    s = gbbc_partition_info()
+    _check(load().bc_partition_info(handle, ctypes.byref(s)), handle)
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def bc_read_border_matrix(handle, p):
+    """(border ids, BM [b, b] int32, sigmaM mod 2^64 [b, b] uint64, overflow [b, b] uint8) of part p."""
+    lib = load()
+    cnt = ctypes.c_int64()
+    _check(lib.bc_read_border_matrix(handle, int(p), ctypes.byref(cnt), None, None, None, None), handle)
+    b = cnt.value
+    ids = np.zeros(max(b, 1), np.int32)
+    bm = np.zeros((b, b), np.int32)
+    sm = np.zeros((b, b), np.uint64)
+    ov = np.zeros((b, b), np.uint8)
+    if b:
+        _check(lib.bc_read_border_matrix(handle, int(p), None, ids.ctypes.data, bm.ctypes.data, sm.ctypes.data,
+                                         ov.ctypes.data), handle)
+    return ids[:b].copy(), bm, sm, ov
+
+
+def bc_compute_partitioned(handle, sources, stream=None):
+    src = _as_i32(sources)
+    p, keep = _ptr(src)
+    _check(load().bc_compute_partitioned(handle, p, len(src), _stream(stream)), handle)
 
 
 def bc_read_source_state(handle, source_index, n):
@@ -520,6 +591,27 @@ class BC:
     def read_fixed(self, graph_id=-1, stream=None):
         n = self.n if graph_id < 0 else int(self.offsets[graph_id + 1] - self.offsets[graph_id])
         return bc_read_fixed(self.h, n, graph_id, stream)
+
+    def read_fixed_into(self, out, graph_id=-1, stream=None):
+        return bc_read_fixed_into(self.h, out, graph_id, stream)
+
+    def add_fixed(self, partial, graph_id=-1, stream=None):
+        bc_add_fixed(self.h, partial, graph_id, stream)
+        return self
+
+    def partition(self, part=None, P=2, stream=None):
+        bc_partition(self.h, part, P, stream)
+        return self
+
+    def partition_info(self):
+        return bc_partition_info(self.h)
+
+    def border_matrix(self, p):
+        return bc_read_border_matrix(self.h, p)
+
+    def compute_partitioned(self, sources, stream=None):
+        bc_compute_partitioned(self.h, sources, stream=stream)
+        return self
 
     def source_state(self, i):
         return bc_read_source_state(self.h, i, self.n)

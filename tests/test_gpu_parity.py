@@ -486,20 +486,37 @@ def test_autotuner_takes_block_schedule_when_batches_fill_the_gpu(gb):
 
 
 def test_fixed_point_partials_add_to_identical_bits(gb):
+    # three shards on three handles (grid and block schedules), their exact
+    # partials added into the first handle by the library (bc_add_fixed, one
+    # partial from host memory and one from device memory): the bits of one
+    # handle over all sources, and the reference helper's exact sum
+    import torch
+    from oracle import fixed as fx
     from paper_2008_05718_gb300 import multirank as mr
     g = gg.rmat(12, 16, seed=91)
     S = gg.sample_sources(g.n, 300, seed=91)
     with gb.BC.from_graph(g) as bc:
         bc.compute(S)
         whole_fixed, whole = bc.read_fixed(), bc.read()
-    parts = []
-    for r in range(3):
-        with gb.BC.from_graph(g, schedule="block" if r % 2 else "grid") as bc:
-            bc.compute(mr.shard(S, r, 3))
-            parts.append(bc.read_fixed())
-    total = mr.sum_fixed(parts)
-    assert np.array_equal(total, whole_fixed)
-    assert np.array_equal(mr.fixed_to_double(total), whole)
+    hs = [gb.BC.from_graph(g, schedule="block" if r % 2 else "grid") for r in range(3)]
+    try:
+        parts = []
+        for r, h in enumerate(hs):
+            h.compute(mr.shard(S, r, 3))
+            parts.append(h.read_fixed())
+        dev = torch.empty(2 * g.n, dtype=torch.int64, device="cuda")
+        hs[2].read_fixed_into(dev)
+        hs[0].add_fixed(parts[1])  # host numpy
+        hs[0].add_fixed(dev)       # device tensor
+        assert np.array_equal(hs[0].read_fixed(), whole_fixed)
+        assert np.array_equal(hs[0].read(), whole)
+        assert fx.sum_parts(parts) == fx.to_int(whole_fixed)
+        assert np.array_equal(fx.to_double(fx.to_int(whole_fixed)), whole)
+        with pytest.raises(gb.GbbcError):
+            hs[1].add_fixed(parts[1], graph_id=3)
+    finally:
+        for h in hs:
+            h.close()
 
 
 # ---- the remaining workloads at full size (sampled sources) ------------------
