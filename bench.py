@@ -90,8 +90,8 @@ def parse():
                     help="batches the grid schedule runs at once (0: the library's default)")
     ap.add_argument("--grouping", default="learned", choices=["learned", "none"],
                     help="order sources by the shipped grouping network before packing them into words")
-    ap.add_argument("--host-loop", action="store_true",
-                    help="grid schedule: drive the level loop from the host instead of the persistent kernel")
+    ap.add_argument("--device-loop", action="store_true",
+                    help="grid schedule: run the level loop in the persistent kernel instead of from the host")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0,
@@ -308,7 +308,7 @@ def run_ours(args):
     out = torch.zeros(g.n, dtype=torch.float64, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     opts = dict(batch_width=args.width, policy=args.policy, streams=args.streams, schedule=args.schedule,
-                flags=gbbc.GBBC_HOST_LOOP if args.host_loop else 0)
+                flags=gbbc.GBBC_DEVICE_LOOP if args.device_loop else 0)
 
     weights = None
     if args.policy in ("auto", "learned") and args.width != 1:

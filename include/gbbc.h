@@ -73,16 +73,18 @@ enum gbbc_flags {
                                   every forward level (the step is run top-down,
                                   undone, then run bottom-up); results are
                                   unchanged, only slower */
-    GBBC_HOST_LOOP = 1u << 3   /* grid schedule: drive the level loop from the
-                                  host (per-step kernels, a counter read-back
-                                  per level, concurrent batches on host
-                                  threads) instead of the persistent kernel,
-                                  as tracing and kept state do; same bits */
+    GBBC_DEVICE_LOOP = 1u << 3, /* grid schedule: run the level loop on the
+                                  device, in one persistent cooperative launch
+                                  per call (see GBBC_SCHEDULE_GRID); same bits */
+    GBBC_SYNC_BACKWARD = 1u << 4 /* bc_compute_partitioned: level-synchronous
+                                  backward over the whole graph instead of the
+                                  asynchronous per-part backward; same bits */
 };
 
 typedef struct gbbc_options {
     uint32_t struct_size;  /* sizeof(gbbc_options); set by bc_options_init */
-    int32_t batch_width;   /* sources per bitset word: 0 = auto, 1 = plain
+    int32_t batch_width;   /* sources per bitset word: 0 = automatic (64, or
+                              tuned; see autotuning), 1 = plain
                               one-source-at-a-time kernels, 32 or 64 */
     int32_t policy;        /* enum gbbc_policy */
     int32_t validate;      /* 1: check CSR symmetry, sorted rows, no loops or
@@ -95,8 +97,9 @@ typedef struct gbbc_options {
                               GBBC_ERR_TIMEOUT (the handle's BC is then
                               undefined until bc_reset); 0 = default, 10^8 */
     uint32_t flags;        /* enum gbbc_flags */
-    int32_t heavy_degree;  /* rows longer than this are processed by a whole
-                              thread block; 0 = default */
+    int32_t heavy_degree;  /* rows longer than this are split into chunk
+                              tasks of 1024 entries, a thread block each;
+                              0 = automatic: 1024, or tuned (see autotuning) */
     int64_t mem_limit_bytes; /* 0 = no limit; else allocations beyond this
                                 many bytes fail with GBBC_ERR_OOM */
     int32_t schedule;      /* enum gbbc_schedule */
@@ -119,14 +122,18 @@ enum gbbc_schedule {
                                 GPU, else the first call times some batches in
                                 both modes (results kept) and the faster mode
                                 is kept for the handle */
-    GBBC_SCHEDULE_GRID = 1,  /* batches on the whole GPU: one persistent
-                                cooperative launch per call runs up to
-                                `streams` batches at once (8 by default), each
-                                batch one level step per tick, the level loop
-                                on the device between grid-wide barriers;
-                                with tracing, kept state or GBBC_HOST_LOOP
-                                the host drives the loop instead (a kernel
-                                per level step, a read-back per level) */
+    GBBC_SCHEDULE_GRID = 1,  /* batches on the whole GPU.  By default the host
+                                drives the level loop: a kernel per level
+                                step, a counter read-back per level, up to
+                                `streams` batches at once (8 by default) on
+                                their own streams and host threads.  With
+                                GBBC_DEVICE_LOOP (or when the autotuner picks
+                                it) one persistent cooperative launch per call
+                                runs the loop on the device instead: up to
+                                `streams` batches in flight, each one level
+                                step per tick, the ticks separated by
+                                grid-wide barriers bounded by timeout_spins.
+                                Tracing and kept state use the host loop */
     GBBC_SCHEDULE_BLOCK = 2, /* one thread-block cluster (1 to 8 blocks) per
                                 batch, many batches at once, one persistent
                                 launch per call; the level loop runs on the
@@ -141,6 +148,18 @@ enum gbbc_schedule {
                                 rounding, bit for bit while path counts stay
                                 below 2^64 */
 };
+
+/*
+ * Autotuning.  When batch_width and heavy_degree are both left automatic,
+ * a handle's first call with at least 2560 sources on one graph of the grid
+ * schedule (above 65,536 vertices, average degree above 6, or the grid
+ * schedule chosen) times five launch configurations on spread blocks of 64
+ * of its sources (width 64 with heavy-row thresholds 1024, 512, 2048; width
+ * 32; the persistent kernel) and keeps the fastest for the handle
+ * (bc_get_stats: batch_width, tuned_heavy_degree, tuned_device_loop).  The
+ * trial sources are part of the call's work; BC does not depend on the
+ * configuration.
+ */
 
 /* Fill *opt with defaults (auto width, auto policy, no validation). */
 void bc_options_init(gbbc_options* opt);
@@ -264,6 +283,9 @@ typedef struct gbbc_stats {
                                the launch stream around each launch) */
     int32_t persist_slots;  /* batches in flight in the last such launch */
     int32_t persist_blocks; /* its cooperative grid */
+    int32_t tuned_heavy_degree; /* heavy-row threshold the autotuner chose (0:
+                               not tuned); batch_width holds its width */
+    int32_t tuned_device_loop;  /* 1 when it chose the persistent kernel */
 } gbbc_stats;
 
 gbbc_status bc_get_stats(const gbbc_graph* g, gbbc_stats* out);
@@ -431,7 +453,8 @@ gbbc_status bc_grouping_scores(gbbc_graph* g, const int32_t* sources, int64_t k,
  * border matrices (Sec. IV-B): BM_p[i][j] = length of a shortest path from
  * border node i to border node j of part p inside p (-1: none), and
  * sigmaM_p[i][j] = the number of such paths (Sec. V-A), by BFS inside the
- * part from every border node.  Single-graph, unweighted handles only.
+ * part from every border node.  Single-graph, unweighted handles only;
+ * 1 <= P <= 32.
  * Errors: GBBC_ERR_INVALID (weighted or multi-graph handle, P, part values),
  * GBBC_ERR_OOM (the border matrices, sum of |B_p|^2 entries, do not fit).
  */
@@ -444,6 +467,8 @@ typedef struct gbbc_partition_info {
     int64_t intra_entries;     /* CSR entries inside parts */
     int64_t matrix_entries;    /* sum over parts of |B_p|^2 */
     int64_t refinement_sweeps; /* Steps 2-5 sweeps of the last bc_compute_partitioned */
+    int64_t backward_waits;    /* waits of one part for another in the asynchronous
+                                  backward phases of that call */
 } gbbc_partition_info;
 
 gbbc_status bc_partition_info(const gbbc_graph* g, gbbc_partition_info* out);
@@ -472,7 +497,14 @@ gbbc_status bc_read_border_matrix(gbbc_graph* g, int32_t p, int64_t* nodes, int3
  *   Step 6     relaxation: BFS inside every part from the source and from
  *              the border nodes entering at their refined distances with
  *              those counts, giving every vertex its distance and sigma;
- * then the backward phase (Eq. 2) over the whole graph.  dist and sigma (mod
+ * then the asynchronous backward phase (Sec. V-B, Eq. 2): each part walks
+ * its own levels, deepest first, on its own group of blocks of one
+ * cooperative launch, and waits for another part only at a level where one
+ * of its border nodes has a successor in that part one level deeper, until
+ * that part has finished the deeper level (every wait bounded by
+ * timeout_spins: GBBC_ERR_TIMEOUT, the handle's BC then undefined until
+ * bc_reset); with GBBC_SYNC_BACKWARD the backward runs level-synchronously
+ * over the whole graph instead.  At most 32 parts.  dist and sigma (mod
  * 2^64, with the overflow flag) equal bc_compute's bit for bit, and so does
  * BC while counts stay below 2^64 (beyond, the wide counts are products
  * rounded to 64-bit mantissas: BC agrees to rounding).  GBBC_KEEP_STATE

@@ -25,6 +25,11 @@
 
 using namespace gbbc;
 
+// Default bound on a device-side wait, in polls (options.timeout_spins = 0).
+#ifndef GBBC_DEFAULT_SPINS
+#define GBBC_DEFAULT_SPINS 100000000LL
+#endif
+
 extern "C" const char* bc_status_string(gbbc_status s);
 extern "C" void bc_graph_destroy(gbbc_graph* g);
 extern "C" gbbc_status bc_clear_trace(gbbc_graph* g);
@@ -80,6 +85,12 @@ struct gbbc_graph {
     unsigned* d_next = nullptr;
     unsigned long long* d_bstats = nullptr;
     int tuned_schedule = 0;  // autotuner's choice (0: not tuned yet)
+    // autotuning of the grid schedule's batch width, heavy-row threshold and
+    // level loop (options left automatic)
+    bool auto_width = false, auto_heavy = false;
+    bool tuned_device = false;       // the persistent kernel runs the grid schedule
+    bool tuned = false;              // the trials have run
+    int cap_heavy_degree = 1024;     // the slots' heavy-row capacities are sized for this threshold
     // tracing (GBBC_TRACE)
     std::vector<gbbc_level_trace> trace;
     gbbc_kernel_profile prof[5];
@@ -142,6 +153,15 @@ struct gbbc_graph {
         int* changed = nullptr;
         int32_t* lane_b = nullptr;      // [64] border index of each lane's source
         long long sweeps = 0;           // refinement sweeps of the last bc_compute_partitioned
+        // asynchronous backward: per-(vertex, lane) distances, the per-(part,
+        // level) waits, the parts' progress, error word and group barriers
+        int32_t* dist = nullptr;        // [n][64]
+        unsigned* need = nullptr;       // [P][n + 1]
+        int* done = nullptr;            // [P]
+        unsigned* ctl = nullptr;        // [2 + 2P]
+        long long* off = nullptr;       // [n + 2] level boundaries of the batch
+        int blocks = 0;                 // cooperative grid of the backward
+        long long waits = 0;            // cross-part waits of the last bc_compute_partitioned
     } pt;
 };
 
@@ -341,8 +361,12 @@ gbbc_status read_options(gbbc_graph* g, const gbbc_options* opt) {
     if (o.schedule < GBBC_SCHEDULE_AUTO || o.schedule > GBBC_SCHEDULE_PAIR)
         return fail(g, GBBC_ERR_INVALID, "unknown schedule %d", o.schedule);
     if (o.streams < 0 || o.streams > 16) return fail(g, GBBC_ERR_INVALID, "streams must be in [0, 16]");
+    g->auto_width = g->opt.batch_width == 0;
+    g->auto_heavy = g->opt.heavy_degree == 0;
     if (g->opt.heavy_degree == 0) g->opt.heavy_degree = 1024;
     if (g->opt.heavy_degree < 32) g->opt.heavy_degree = 32;
+    // the smallest threshold the autotuner may try sizes the heavy-row lists
+    g->cap_heavy_degree = g->auto_heavy ? 512 : g->opt.heavy_degree;
     return GBBC_OK;
 }
 
@@ -410,7 +434,7 @@ gbbc_status alloc_slot_into(gbbc_graph* g, Slot& s) {
     long long hcap = 1, tcap = 1;
     for (int32_t v = 0; v < g->n; ++v) {
         long long d = (long long)g->h_row_ptr[v + 1] - g->h_row_ptr[v];
-        if (d > g->opt.heavy_degree) {
+        if (d > g->cap_heavy_degree) {
             hcap += 1;
             tcap += (d + kChunk - 1) / kChunk;
         }
@@ -944,7 +968,8 @@ void free_partition(gbbc_graph* g) {
                     (void*)q.SM.mod, (void*)q.SM.N, (void*)q.SM.X, (void*)q.SM.big, (void*)q.D, (void*)q.D1,
                     (void*)q.S1.mod, (void*)q.S1.N, (void*)q.S1.X, (void*)q.S1.big, (void*)q.A.mod, (void*)q.A.N,
                     (void*)q.A.X, (void*)q.A.big, (void*)q.Sig.mod, (void*)q.Sig.N, (void*)q.Sig.X,
-                    (void*)q.Sig.big, (void*)q.changed, (void*)q.lane_b})
+                    (void*)q.Sig.big, (void*)q.changed, (void*)q.lane_b, (void*)q.dist, (void*)q.need,
+                    (void*)q.done, (void*)q.ctl, (void*)q.off})
         dfree(g, p);
     q = gbbc_graph::Part();
 }
@@ -996,6 +1021,46 @@ struct SeedHooks : FwdHooks {
         return GBBC_OK;
     }
 };
+
+// The asynchronous backward phase (Sec. V-B): every part walks its own
+// levels on its own group of blocks and waits only where a border node's
+// successor lies in another part one level deeper (bc_partition.cu).
+gbbc_status part_backward_async(gbbc_graph* g, const Csr& call, const std::vector<long long>& off, bool wide,
+                                cudaStream_t st) {
+    gbbc_graph::Part& q = g->pt;
+    const int nlev = (int)off.size() - 1;
+    if (nlev < 2) return GBBC_OK;
+    const int P = q.P;
+    if (q.blocks == 0) {
+        const int per_sm = part_backward_blocks_per_sm();
+        if (per_sm < 1) return fail(g, GBBC_ERR_CUDA, "partitioned backward: occupancy query failed");
+        q.blocks = per_sm * g->nsm;
+        if (q.blocks < P) return fail(g, GBBC_ERR_INVALID, "partitioned backward: %d parts need %d blocks", P, P);
+    }
+    const size_t n = (size_t)std::max<int32_t>(g->n, 1);
+    CK(g, cudaMemsetAsync(q.dist, 0xff, n * kLanes * sizeof(int32_t), st));
+    for (int l = 0; l < nlev; ++l) launch_part_dist(g->slot, off[l], off[l + 1], l, q.dist, g->nsm, st);
+    CK(g, cudaMemsetAsync(q.need, 0, (size_t)P * nlev * sizeof(unsigned), st));
+    for (int l = 1; l < nlev; ++l)
+        launch_part_need(g->slot, off[l], off[l + 1], l, nlev, q.dist, q.part, q.bidx, q.cut_rp, q.cut_col, q.need,
+                         g->nsm, st);
+    CK(g, cudaMemcpyAsync(q.off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+    launch_fill_i32(q.done, P, nlev, st);
+    CK(g, cudaMemsetAsync(q.ctl, 0, (size_t)(2 + 2 * P) * sizeof(unsigned), st));
+    const long long spins = g->opt.timeout_spins > 0 ? (long long)g->opt.timeout_spins : GBBC_DEFAULT_SPINS;
+    CK(g, launch_part_backward(call, g->slot, q.dist, q.part, P, q.off, nlev, q.need, q.done, q.ctl, g->d_bc, spins,
+                               wide, q.blocks, st));
+    g->stats.kernel_launches += 2 * nlev + 1;
+    unsigned hc[2] = {0u, 0u};
+    CK(g, cudaMemcpyAsync(hc, q.ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    CK(g, cudaStreamSynchronize(st));
+    if (hc[0] & 1u)
+        return fail(g, GBBC_ERR_TIMEOUT,
+                    "partitioned backward: a wait passed timeout_spins=%lld polls; the handle's BC is undefined until "
+                    "bc_reset", spins);
+    q.waits += hc[1];
+    return GBBC_OK;
+}
 
 // One batch by the partitioned method: Step 1, Steps 2-5, border sigma,
 // Step 6, kept state, backward over the whole graph.
@@ -1054,8 +1119,12 @@ gbbc_status part_batch(gbbc_graph* g, const BatchDesc& b, cudaStream_t st) {
         launch_keep_sigma(g->slot, b.lo, b.hi, g->k_sigma, g->k_ovf, g->n, b.first, b.nsrc, st);
         g->stats.kernel_launches += nlev + 1;
     }
-    // backward phase over the whole graph (successors across border edges too)
-    CKS(run_backward(g, call, g->slot, off, wide, g->d_bc, g->stats, st));
+    if (g->opt.flags & GBBC_SYNC_BACKWARD) {
+        // level-synchronous backward over the whole graph
+        CKS(run_backward(g, call, g->slot, off, wide, g->d_bc, g->stats, st));
+    } else {
+        CKS(part_backward_async(g, call, off, wide, st));
+    }
     if (wide) g->stats.wide_batches++;
     g->stats.batches++;
     g->stats.sources += b.nsrc;
@@ -1156,6 +1225,105 @@ gbbc_status compute_impl(gbbc_graph* g, const std::vector<int32_t>& gsrc, const 
     return compute_batched(g, gsrc, gid, st, false);
 }
 
+bool grid_graph(const gbbc_graph* g, const BatchDesc& b);
+gbbc_status run_grid_batches(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaStream_t st);
+gbbc_status persist_prepare(gbbc_graph* g, int W);
+double now_s();
+int grid_workers(gbbc_graph* g, size_t nb);
+gbbc_status ensure_workers(gbbc_graph* g, int count);
+
+// Autotuning of the grid schedule (a handle's first call with at least
+// kTuneMinSources sources on one large graph, width and heavy-row threshold
+// left automatic): five configurations -- width 64 with heavy-row thresholds
+// 1024, 512 and 2048, width 32 with 1024, and width 64 with 1024 on the
+// persistent kernel (the device loop) -- each run kTuneBlocks blocks of 64
+// consecutive sources of the call's ordered list (grouped and sorted by the
+// grouping network when it is loaded).  The 5 x kTuneBlocks blocks sit at
+// evenly spaced positions of the list and are dealt to the configurations
+// in turn, so every configuration sees sources from the whole range; the
+// one with the most sources per second is kept for the handle.  Trial
+// sources count once, like any other (BC is an exact integer sum).  This is
+// the measure-then-split idea of the paper's variable partitioning (Sec.
+// V-D) applied to the launch configuration.
+constexpr int kTuneBlocks = 4;
+constexpr int kTuneConfigs = 5;
+constexpr long long kTuneMinSources = 2LL * kTuneConfigs * kTuneBlocks * kLanes;
+
+bool tune_wanted(gbbc_graph* g, const std::vector<int32_t>& gid, long long k) {
+    if (g->tuned || !g->auto_width || !g->auto_heavy || g->k_dist || (g->opt.flags & (GBBC_TRACE | GBBC_DEVICE_LOOP)))
+        return false;
+    if (g->goff.size() != 2 || k < kTuneMinSources) return false;
+    if (!(g->opt.schedule == GBBC_SCHEDULE_AUTO || g->opt.schedule == GBBC_SCHEDULE_GRID)) return false;
+    BatchDesc b;
+    b.gi = 0;
+    b.lo = 0;
+    b.hi = g->n;
+    (void)gid;
+    return g->opt.schedule == GBBC_SCHEDULE_GRID || grid_graph(g, b);
+}
+
+gbbc_status autotune(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<long long>& order,
+                     std::vector<char>& taken, cudaStream_t st) {
+    struct Cfg {
+        int width, heavy;
+        bool device;
+    };
+    const Cfg cfgs[kTuneConfigs] = {{64, 1024, false}, {64, 512, false}, {64, 2048, false}, {32, 1024, false},
+                                    {64, 1024, true}};
+    const long long k = (long long)order.size();
+    const int nblk = kTuneConfigs * kTuneBlocks;
+    std::vector<std::vector<int32_t>> src(kTuneConfigs);
+    for (int j = 0; j < nblk; ++j) {
+        long long start = (long long)(((double)j + 0.5) * (double)k / nblk) - kLanes / 2;
+        start = std::max(0LL, std::min(start, k - kLanes));
+        for (long long p = start; p < start + kLanes; ++p)
+            if (!taken[p]) {
+                taken[p] = 1;
+                src[j % kTuneConfigs].push_back(gsrc[order[p]]);
+            }
+    }
+    // one-time set-up outside the timed trials
+    CKS(alloc_slot(g));
+    const int W = grid_workers(g, 64);
+    CKS(ensure_workers(g, W - 1));
+    CKS(persist_prepare(g, std::min(W, kMaxPSlots)));
+    double best_rate = -1.0;
+    int best = 0;
+    for (int c = 0; c < kTuneConfigs; ++c) {
+        g->opt.batch_width = cfgs[c].width;
+        g->opt.heavy_degree = cfgs[c].heavy;
+        g->tuned_device = cfgs[c].device;
+        std::vector<BatchDesc> bs;
+        for (size_t i = 0; i < src[c].size();) {
+            BatchDesc b;
+            b.gi = 0;
+            b.lo = 0;
+            b.hi = g->n;
+            b.first = 0;
+            b.nsrc = 0;
+            while (i < src[c].size() && b.nsrc < cfgs[c].width) b.src[b.nsrc++] = src[c][i++];
+            bs.push_back(b);
+        }
+        CK(g, cudaStreamSynchronize(st));
+        const double t0 = now_s();
+        CKS(run_grid_batches(g, bs.data(), bs.size(), st));
+        CK(g, cudaStreamSynchronize(st));
+        const double rate = (double)src[c].size() / std::max(now_s() - t0, 1e-9);
+        if (rate > best_rate) {
+            best_rate = rate;
+            best = c;
+        }
+    }
+    g->opt.batch_width = cfgs[best].width;
+    g->opt.heavy_degree = cfgs[best].heavy;
+    g->tuned_device = cfgs[best].device;
+    g->tuned = true;
+    g->stats.batch_width = cfgs[best].width;
+    g->stats.tuned_heavy_degree = cfgs[best].heavy;
+    g->stats.tuned_device_loop = cfgs[best].device ? 1 : 0;
+    return GBBC_OK;
+}
+
 // The bitset schedules (grid, block): sources packed 64 (or 32) per word.
 gbbc_status compute_batched(gbbc_graph* g, const std::vector<int32_t>& gsrc, const std::vector<int32_t>& gid,
                             cudaStream_t st, bool mixed) {
@@ -1180,6 +1348,16 @@ gbbc_status compute_batched(gbbc_graph* g, const std::vector<int32_t>& gsrc, con
         });
     } else {
         std::stable_sort(order.begin(), order.end(), [&](long long a, long long b) { return gid[a] < gid[b]; });
+    }
+    if (tune_wanted(g, gid, k)) {  // trial runs on spread blocks of the list, then the rest
+        std::vector<char> taken((size_t)k, 0);
+        CKS(autotune(g, gsrc, order, taken, st));
+        std::vector<long long> rest;
+        rest.reserve((size_t)k);
+        for (long long i = 0; i < k; ++i)
+            if (!taken[i]) rest.push_back(order[i]);
+        order.swap(rest);
+        k = (long long)order.size();
     }
     std::vector<BatchDesc> batches;
     const int width = g->opt.batch_width == 32 ? 32 : kLanes;
@@ -1627,13 +1805,15 @@ gbbc_status run_persistent(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaSt
                            std::vector<BatchDesc>& wide_out);
 gbbc_status run_grid_host(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaStream_t st);
 
-// The grid schedule: the persistent kernel for narrow batches, unless the
-// level loop must run on the host (tracing, kept state, GBBC_HOST_LOOP), in
-// which case (and for batches in the wide format) the host drives it.
+// The grid schedule: the host-driven level loop, or the persistent kernel for
+// narrow batches when GBBC_DEVICE_LOOP is set or the autotuner chose it
+// (never with tracing or kept state, which need the host loop); batches in
+// the wide format always run the host loop.
 gbbc_status run_grid_batches(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaStream_t st) {
     if (nb == 0) return GBBC_OK;
-    const bool host_loop = (g->opt.flags & (GBBC_TRACE | GBBC_HOST_LOOP)) || g->k_dist;
-    if (host_loop) return run_grid_host(g, bs, nb, st);
+    const bool device = ((g->opt.flags & GBBC_DEVICE_LOOP) || g->tuned_device) &&
+                        !(g->opt.flags & GBBC_TRACE) && !g->k_dist;
+    if (!device) return run_grid_host(g, bs, nb, st);
     std::vector<BatchDesc> narrow, wide;
     for (size_t i = 0; i < nb; ++i) (g->wide_graph[bs[i].gi] ? wide : narrow).push_back(bs[i]);
     CKS(run_persistent(g, narrow.data(), narrow.size(), st, wide));
@@ -1693,14 +1873,11 @@ gbbc_status run_grid_host(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaStr
 // call in one cooperative launch, W batches in flight on W slots (the handle's
 // slot and the workers' slots), the level loop on the device.  Batches whose
 // counts reach 2^64 come back in a list and are rerun wide by the host loop.
-#ifndef GBBC_DEFAULT_SPINS
-#define GBBC_DEFAULT_SPINS 100000000LL
-#endif
-gbbc_status run_persistent(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaStream_t st,
-                           std::vector<BatchDesc>& wide_out) {
-    if (nb == 0) return GBBC_OK;
+// One-time set-up of the persistent kernel for W slots: the slots, the
+// device copies of their descriptors and control words, level boundaries,
+// events and the cooperative grid size.
+gbbc_status persist_prepare(gbbc_graph* g, int W) {
     CKS(alloc_slot(g));
-    const int W = std::max(1, std::min(grid_workers(g, nb), kMaxPSlots));
     CKS(ensure_workers(g, W - 1));
     if (g->p_blocks == 0) {
         const int per_sm = persist_blocks_per_sm();
@@ -1719,6 +1896,19 @@ gbbc_status run_persistent(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaSt
         CKS(dalloc_t(g, &g->p_lev, (size_t)W * n2));
         g->p_lev_rows = W;
     }
+    if (!g->p_ev[0]) {
+        CK(g, cudaEventCreate(&g->p_ev[0]));
+        CK(g, cudaEventCreate(&g->p_ev[1]));
+    }
+    return GBBC_OK;
+}
+
+gbbc_status run_persistent(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaStream_t st,
+                           std::vector<BatchDesc>& wide_out) {
+    if (nb == 0) return GBBC_OK;
+    const int W = std::max(1, std::min(grid_workers(g, nb), kMaxPSlots));
+    CKS(persist_prepare(g, W));
+    const size_t n2 = (size_t)std::max<int32_t>(g->n, 1) + 2;
     if (g->p_wide_cap < (long long)nb) {
         dfree(g, g->p_wide);
         g->p_wide = nullptr;
@@ -1766,10 +1956,6 @@ gbbc_status run_persistent(gbbc_graph* g, const BatchDesc* bs, size_t nb, cudaSt
     CK(g, cudaMemcpyAsync(g->d_bsrc, hsrc.data(), hsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     const long long spins = g->opt.timeout_spins > 0 ? (long long)g->opt.timeout_spins : GBBC_DEFAULT_SPINS;
     Csr c{g->n, g->nnz, g->d_row_ptr, g->d_col};
-    if (!g->p_ev[0]) {
-        CK(g, cudaEventCreate(&g->p_ev[0]));
-        CK(g, cudaEventCreate(&g->p_ev[1]));
-    }
     CK(g, cudaEventRecord(g->p_ev[0], st));
     CK(g, launch_persist(c, g->p_slots, W, g->p_ctl, g->p_lev, (long long)n2, g->d_bb, (int)nb, g->d_bsrc, g->d_bc,
                          effective_policy(g), g->d_policy, g->d_graph_max_deg, g->opt.heavy_degree, spins, g->p_glob,
@@ -2427,7 +2613,8 @@ gbbc_status bc_partition(gbbc_graph* g, const int32_t* part, int32_t P, void* st
     if (!g) return GBBC_ERR_INVALID;
     if (g->goff.size() != 2 || g->d_w)
         return fail(g, GBBC_ERR_INVALID, "bc_partition: single-graph, unweighted handles only");
-    if (P < 1 || P > std::max<int32_t>(g->n, 1)) return fail(g, GBBC_ERR_INVALID, "bc_partition: P = %d", P);
+    if (P < 1 || P > std::max<int32_t>(g->n, 1) || P > kMaxParts)
+        return fail(g, GBBC_ERR_INVALID, "bc_partition: P = %d (1 to %d, at most n)", P, kMaxParts);
     cudaStream_t st = (cudaStream_t)stream;
     const int32_t n = g->n;
     std::vector<int32_t> hp;
@@ -2493,6 +2680,11 @@ gbbc_status bc_partition(gbbc_graph* g, const int32_t* part, int32_t P, void* st
     CKS(alloc_wide_arr(g, q.Sig, c1));
     CKS(dalloc_t(g, &q.changed, 1));
     CKS(dalloc_t(g, &q.lane_b, kLanes));
+    CKS(dalloc_t(g, &q.dist, n1 * kLanes));
+    CKS(dalloc_t(g, &q.need, (size_t)P * (n1 + 1)));
+    CKS(dalloc_t(g, &q.done, (size_t)P));
+    CKS(dalloc_t(g, &q.ctl, (size_t)(2 + 2 * P)));
+    CKS(dalloc_t(g, &q.off, n1 + 2));
     q.in_nnz = (long long)in_col.size();
     q.cut_nnz = (long long)cut_col.size();
     q.nbt = nbt;
@@ -2548,6 +2740,7 @@ gbbc_status bc_partition_info(const gbbc_graph* g, gbbc_partition_info* out) {
     out->intra_entries = g->pt.in_nnz;
     out->matrix_entries = g->pt.P ? g->pt.h_moff.back() : 0;
     out->refinement_sweeps = g->pt.sweeps;
+    out->backward_waits = g->pt.waits;
     return GBBC_OK;
 }
 
@@ -2583,6 +2776,7 @@ gbbc_status bc_compute_partitioned(gbbc_graph* g, const int32_t* sources, int64_
     CKS(alloc_slot(g));
     g->last_stream = st;
     g->pt.sweeps = 0;
+    g->pt.waits = 0;
     const int width = g->opt.batch_width == 32 ? 32 : kLanes;
     for (long long i = 0; i < k; i += width) {
         BatchDesc b;

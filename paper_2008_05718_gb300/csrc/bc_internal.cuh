@@ -230,6 +230,18 @@ void launch_seed_inject(const Slot& s, int level, const int32_t* border, long lo
 void launch_seed_add(const Slot& s, int level, const int32_t* border, long long nbt, const int32_t* D,
                      const PartWide& A, bool wide, int nsm, cudaStream_t st);
 
+// the asynchronous backward of the partitioned method (at most 32 parts)
+constexpr int kMaxParts = 32;
+int part_backward_blocks_per_sm();
+void launch_part_dist(const Slot& s, long long q_lo, long long q_hi, int level, int32_t* dist, int nsm,
+                      cudaStream_t st);
+void launch_part_need(const Slot& s, long long q_lo, long long q_hi, int level, int nlev, const int32_t* dist,
+                      const int32_t* part, const int32_t* bidx, const int32_t* cut_rp, const int32_t* cut_col,
+                      unsigned* need, int nsm, cudaStream_t st);
+cudaError_t launch_part_backward(const Csr& g, const Slot& s, const int32_t* dist, const int32_t* part, int P,
+                                 const long long* off, int nlev, const unsigned* need, int* done, unsigned* ctl,
+                                 u64* bc, long long spin_limit, bool wide, int blocks, cudaStream_t st);
+
 // ---- launch wrappers (bc_kernels.cu) ----
 void launch_seed(const Slot& s, int nsrc, cudaStream_t st);
 void launch_push(const Csr& g, const Slot& s, long long q_lo, long long q_hi, int level, int heavy_deg,

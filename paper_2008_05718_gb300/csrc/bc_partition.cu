@@ -476,4 +476,225 @@ void launch_seed_add(const Slot& s, int level, const int32_t* border, long long 
     k_seed_add<<<grid_of(nbt * kLanes, nsm), kBlock, 0, st>>>(s, level, border, nbt, D, a, wide);
 }
 
+// ---- the asynchronous backward phase (Sec. V-B) ------------------------------
+// After Step 6 every part walks its own levels from the deepest one up, on its
+// own group of blocks, and waits for another part only at a level where one of
+// its border nodes has a successor in that part one level deeper
+// (need[p][l], a bit per other part): the wait ends once that part has
+// finished the deeper level (done[q] <= l + 1).  The part with the deepest
+// pending level never waits, so the waits always end; each is bounded by
+// spin_limit polls all the same (error bit 0, GBBC_ERR_TIMEOUT).
+// Successors are found from per-(vertex, lane) distances: parts run at
+// different levels, so the level-parity frontier words cannot serve them.
+
+// dist[v][j] = level for the entries of one level (lane-minor rows of 64).
+__global__ void k_part_dist(Slot s, long long q_lo, long long q_hi, int level, int32_t* dist) {
+    const int lane = threadIdx.x & 31;
+    for (long long e = q_lo + gwarp(); e < q_hi; e += nwarps()) {
+        const int32_t v = s.qv[e];
+        const u64 m = s.qm[e];
+        if ((m >> lane) & 1ull) dist[(size_t)v * kLanes + lane] = level;
+        if ((m >> (lane + 32)) & 1ull) dist[(size_t)v * kLanes + lane + 32] = level;
+    }
+}
+
+// need[part(v) * nlev + level] |= 1 << part(w) for border entries (v, m) at
+// `level` with a border neighbour w at level + 1 in one of m's lanes.
+__global__ void k_part_need(Slot s, long long q_lo, long long q_hi, int level, int nlev, const int32_t* dist,
+                            const int32_t* part, const int32_t* bidx, const int32_t* cut_rp, const int32_t* cut_col,
+                            unsigned* need) {
+    const int lane = threadIdx.x & 31;
+    for (long long e = q_lo + gwarp(); e < q_hi; e += nwarps()) {
+        const int32_t v = s.qv[e];
+        if (bidx[v] < 0) continue;
+        const u64 m = s.qm[e];
+        unsigned bits = 0u;
+        for (int32_t p = cut_rp[v]; p < cut_rp[v + 1]; ++p) {
+            const int32_t w = cut_col[p];
+            const int32_t* dw = dist + (size_t)w * kLanes;
+            const bool hit = (((m >> lane) & 1ull) && dw[lane] == level + 1) ||
+                             (((m >> (lane + 32)) & 1ull) && dw[lane + 32] == level + 1);
+            if (__any_sync(FULL, hit)) bits |= 1u << part[w];
+        }
+        if (lane == 0 && bits) atomicOr(need + (size_t)part[v] * nlev + level, bits);
+    }
+}
+
+__device__ __forceinline__ unsigned ld_acq(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_acq_i(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_rel_i(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Barrier of the G blocks of one part's group (bar[0] arrivals, bar[1]
+// generation); false when it gave up or an error was reported.
+__device__ __forceinline__ bool group_barrier(unsigned* bar, unsigned G, unsigned* err, long long spin_limit,
+                                              int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen = ld_acq(bar + 1);
+        __threadfence();
+        if (atomicAdd(bar, 1u) == G - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (ld_acq(bar + 1) == gen) {
+                if (ld_acq(err) & 1u) {
+                    ok = 0;
+                    break;
+                }
+                if (++spins >= spin_limit) {
+                    atomicOr(err, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Backward step of entry e at `level` from the distance rows: for each lane
+// j of the entry, the successors are the neighbours w (any part) with
+// dist[w][j] = level + 1; the same fixed-point sums as the level-synchronous
+// backward (bc_fixed.cuh), BC added without atomics (each vertex belongs to
+// one part, whose group runs its levels one after the other).
+template <bool WIDE>
+__device__ __forceinline__ void bwd_entry_dist(const Csr& g, const Slot& s, const int32_t* dist, u64* bc, int level,
+                                               long long e) {
+    const int lane = threadIdx.x & 31;
+    const int32_t v = s.qv[e];
+    const u64 m = s.qm[e];
+    u64 N0, N1;
+    int E0, E1;
+    lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
+    const bool l0 = (m >> lane) & 1ull, l1 = (m >> (lane + 32)) & 1ull;
+    u128 a0 = {0ull, 0ull}, a1 = {0ull, 0ull};
+    for (int32_t p = __ldg(g.row_ptr + v); p < __ldg(g.row_ptr + v + 1); ++p) {
+        const int32_t w = __ldg(g.col + p);
+        const size_t at0 = (size_t)w * kLanes + lane, at1 = at0 + 32;
+        if (l0 && __ldcg(dist + at0) == level + 1)
+            a0 = add128(a0, psi_term<WIDE>(__ldcg(s.psi + at0), WIDE ? __ldcg(s.psi_e + at0) : 0, E0));
+        if (l1 && __ldcg(dist + at1) == level + 1)
+            a1 = add128(a1, psi_term<WIDE>(__ldcg(s.psi + at1), WIDE ? __ldcg(s.psi_e + at1) : 0, E1));
+    }
+    bwd_store<WIDE, false>(s, bc, v, m, E0, E1, N0, N1, a0, a1);
+}
+
+// One cooperative launch: part p runs on blocks [p * G, (p + 1) * G).
+// ctl: [0] error bits, [1] waits performed, [2 + 2p], [3 + 2p] part p's group
+// barrier; done[p] = the last level part p finished (nlev before any).
+template <bool WIDE>
+__global__ void __launch_bounds__(kBlock) k_part_backward(Csr g, Slot s, const int32_t* dist, const int32_t* part,
+                                                          int P, const long long* off, int nlev,
+                                                          const unsigned* need, int* done, unsigned* ctl, u64* bc,
+                                                          long long spin_limit) {
+    __shared__ int s_ok;
+    const unsigned G = gridDim.x / (unsigned)P;
+    const int p = (int)(blockIdx.x / G);
+    if (p >= P) return;
+    const unsigned r = blockIdx.x % G;
+    const long long gw = ((long long)r * blockDim.x + threadIdx.x) >> 5;
+    const long long gnw = ((long long)G * blockDim.x) >> 5;
+    unsigned* err = ctl;
+    unsigned* bar = ctl + 2 + 2 * p;
+    for (int l = nlev - 1; l >= 1; --l) {
+        const unsigned mask = need[(size_t)p * nlev + l] & ~(1u << p);
+        if (mask && threadIdx.x == 0) {  // wait for the parts holding successors one level deeper
+            int ok = 1;
+            long long spins = 0;
+            for (int q = 0; q < P && ok; ++q) {
+                if (!((mask >> q) & 1u)) continue;
+                while (ld_acq_i(done + q) > l + 1) {
+                    if (ld_acq(err) & 1u) {
+                        ok = 0;
+                        break;
+                    }
+                    if (++spins >= spin_limit) {
+                        atomicOr(err, 1u);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            if (r == 0 && ok) atomicAdd(ctl + 1, 1u);
+            s_ok = ok;
+        }
+        if (mask) {
+            __syncthreads();
+            if (!s_ok) return;
+        }
+        const long long q_lo = off[l], q_hi = off[l + 1];
+        for (long long e = q_lo + gw; e < q_hi; e += gnw)
+            if (part[s.qv[e]] == p) bwd_entry_dist<WIDE>(g, s, dist, bc, l, e);
+        if (!group_barrier(bar, G, err, spin_limit, &s_ok)) return;
+        if (r == 0 && threadIdx.x == 0) st_rel_i(done + p, l);
+    }
+}
+
+int part_backward_blocks_per_sm() {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_part_backward<false>, kBlock, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_part_backward<true>, kBlock, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return a < b ? a : b;
+}
+
+void launch_part_dist(const Slot& s, long long q_lo, long long q_hi, int level, int32_t* dist, int nsm,
+                      cudaStream_t st) {
+    if (q_hi <= q_lo) return;
+    long long blocks = ((q_hi - q_lo) * kWarp + kBlock - 1) / kBlock;
+    if (blocks > (long long)nsm * 8) blocks = (long long)nsm * 8;
+    k_part_dist<<<(int)blocks, kBlock, 0, st>>>(s, q_lo, q_hi, level, dist);
+}
+
+void launch_part_need(const Slot& s, long long q_lo, long long q_hi, int level, int nlev, const int32_t* dist,
+                      const int32_t* part, const int32_t* bidx, const int32_t* cut_rp, const int32_t* cut_col,
+                      unsigned* need, int nsm, cudaStream_t st) {
+    if (q_hi <= q_lo) return;
+    long long blocks = ((q_hi - q_lo) * kWarp + kBlock - 1) / kBlock;
+    if (blocks > (long long)nsm * 8) blocks = (long long)nsm * 8;
+    k_part_need<<<(int)blocks, kBlock, 0, st>>>(s, q_lo, q_hi, level, nlev, dist, part, bidx, cut_rp, cut_col, need);
+}
+
+cudaError_t launch_part_backward(const Csr& g, const Slot& s, const int32_t* dist, const int32_t* part, int P,
+                                 const long long* off, int nlev, const unsigned* need, int* done, unsigned* ctl,
+                                 u64* bc, long long spin_limit, bool wide, int blocks, cudaStream_t st) {
+    if (P < 1 || blocks < P) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(blocks / P * P), 1, 1);
+    cfg.blockDim = dim3(kBlock, 1, 1);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (wide)
+        return cudaLaunchKernelEx(&cfg, k_part_backward<true>, g, s, dist, part, P, off, nlev, need, done, ctl, bc,
+                                  spin_limit);
+    return cudaLaunchKernelEx(&cfg, k_part_backward<false>, g, s, dist, part, P, off, nlev, need, done, ctl, bc,
+                              spin_limit);
+}
+
 }  // namespace gbbc

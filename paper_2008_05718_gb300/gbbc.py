@@ -25,7 +25,8 @@ SCHEDULE = {"auto": 0, "grid": 1, "block": 2, "pair": 3}
 GBBC_KEEP_STATE = 1
 GBBC_TRACE = 2
 GBBC_TRACE_BOTH = 4
-GBBC_HOST_LOOP = 8
+GBBC_DEVICE_LOOP = 8
+GBBC_SYNC_BACKWARD = 16
 
 # every symbol include/gbbc.h declares
 EXPORTS = ("bc_options_init", "bc_graph_create", "bc_graph_create_multi", "bc_graph_create_weighted", "bc_compute", "bc_compute_multi",
@@ -53,7 +54,8 @@ class gbbc_stats(ctypes.Structure):
                 ("batch_width", ctypes.c_int32), ("policy", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("block_slots", ctypes.c_int32),
                 ("persist_launches", ctypes.c_int64), ("persist_ms", ctypes.c_double),
-                ("persist_slots", ctypes.c_int32), ("persist_blocks", ctypes.c_int32)]
+                ("persist_slots", ctypes.c_int32), ("persist_blocks", ctypes.c_int32),
+                ("tuned_heavy_degree", ctypes.c_int32), ("tuned_device_loop", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -79,7 +81,7 @@ class gbbc_kernel_profile(ctypes.Structure):
 class gbbc_partition_info(ctypes.Structure):
     _fields_ = [("parts", ctypes.c_int32), ("border_nodes", ctypes.c_int64), ("border_edges", ctypes.c_int64),
                 ("intra_entries", ctypes.c_int64), ("matrix_entries", ctypes.c_int64),
-                ("refinement_sweeps", ctypes.c_int64)]
+                ("refinement_sweeps", ctypes.c_int64), ("backward_waits", ctypes.c_int64)]
 
 
 class GbbcError(RuntimeError):

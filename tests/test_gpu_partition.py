@@ -70,8 +70,8 @@ def test_border_matrices_match_the_definition(gb, name, make, partf):
             assert np.array_equal(sm, exact) and np.array_equal(ov, big)
 
 
-def _partitioned(gb, g, S, part, P, keep=(), **opts):
-    flags = gb.GBBC_KEEP_STATE if keep else 0
+def _partitioned(gb, g, S, part, P, keep=(), flags=0, **opts):
+    flags |= gb.GBBC_KEEP_STATE if keep else 0
     with gb.BC.from_graph(g, flags=flags, **opts) as bc:
         bc.partition(part, P)
         bc.compute_partitioned(S)
@@ -147,3 +147,35 @@ def test_partition_errors(gb):
         with pytest.raises(gb.GbbcError) as e:
             bc.partition(None, 2)
         assert e.value.status == gb.GBBC_ERR_INVALID
+
+
+@pytest.mark.parametrize("name,make,k,P", [("er4096_p4", lambda: gg.workload("er4096")[0], 130, 4),
+                                           ("grid64_p3", lambda: gg.grid(64, "0.05", seed=405), 100, 3),
+                                           ("rmat12_p2", lambda: gg.rmat(12, 16, seed=406), 100, 2)])
+def test_asynchronous_backward_equals_level_synchronous(gb, name, make, k, P):
+    # each part walks its own levels and waits only where a border node's
+    # successor lies in another part one level deeper: the same integer sums
+    g = make()
+    S = gg.sample_sources(g.n, min(k, g.n), seed=43)
+    fx_a, _, _, info_a = _partitioned(gb, g, S, None, P)
+    fx_s, _, _, info_s = _partitioned(gb, g, S, None, P, flags=gb.GBBC_SYNC_BACKWARD)
+    assert np.array_equal(fx_a, fx_s)
+    assert info_a["backward_waits"] > 0 and info_s["backward_waits"] == 0
+    # far fewer waits than parts x levels: a part waits only at levels with a
+    # border successor one level deeper elsewhere
+    assert info_a["backward_waits"] <= P * 64 * ((k + 63) // 64)
+
+
+def test_asynchronous_backward_wait_bound(gb):
+    g = gg.grid(64, "0.05", seed=407)
+    S = gg.sample_sources(g.n, 64, seed=44)
+    with gb.BC.from_graph(g, timeout_spins=1) as bc:
+        bc.partition(None, 4)
+        with pytest.raises(gb.GbbcError) as e:
+            bc.compute_partitioned(S)
+        assert e.value.status == gb.GBBC_ERR_TIMEOUT
+        bc.reset()
+    fx, _, _, _ = _partitioned(gb, g, S, None, 4)
+    with gb.BC.from_graph(g) as bc:
+        bc.compute(S)
+        assert np.array_equal(bc.read_fixed(), fx)

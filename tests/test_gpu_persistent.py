@@ -2,8 +2,9 @@
 batches in flight, the level loop on the device between bounded grid
 barriers.
 
-Its BC must be bit-identical to the host-driven level loop (GBBC_HOST_LOOP:
-per-step kernels, a read-back per level) and agree with the oracle; a grid
+It runs with GBBC_DEVICE_LOOP; its BC must be bit-identical to the default
+host-driven level loop (per-step kernels, a read-back per level) and agree
+with the oracle; a grid
 barrier that waits longer than timeout_spins must end the launch with
 GBBC_ERR_TIMEOUT and leave the handle usable after bc_reset.
 """
@@ -24,7 +25,9 @@ def assert_bc_close(got, want):
     assert excess[i] <= 0, f"vertex {i}: gpu {got[i]!r} oracle {want[i]!r}"
 
 
-def fixed_bits(gb, g, S, **opts):
+def fixed_bits(gb, g, S, device=True, **opts):
+    if device:
+        opts["flags"] = opts.get("flags", 0) | gb.GBBC_DEVICE_LOOP
     with gb.BC.from_graph(g, schedule="grid", **opts) as bc:
         bc.compute(S)
         return bc.read_fixed(), bc.read(), bc.stats()
@@ -46,7 +49,7 @@ def test_persistent_bits_equal_host_loop_and_oracle(gb, name, make, k, opts):
     g = make()
     S = gg.sample_sources(g.n, min(k, g.n), seed=17)
     fx_p, bc_p, st_p = fixed_bits(gb, g, S, **opts)
-    fx_h, _, st_h = fixed_bits(gb, g, S, flags=gb.GBBC_HOST_LOOP, **opts)
+    fx_h, _, st_h = fixed_bits(gb, g, S, device=False, **opts)
     assert np.array_equal(fx_p, fx_h)
     assert st_p["batches"] == st_h["batches"] == (len(S) + 63) // 64
     assert st_p["levels_fwd"] == st_h["levels_fwd"]
@@ -61,7 +64,7 @@ def test_persistent_reruns_wide_batches_on_the_host(gb):
     g = gg.full_grid(70, 70)
     S = np.array([0, 69, 4899, 2450, 100, 1000, 3000], np.int32)
     fx_p, bc_p, st = fixed_bits(gb, g, S)
-    fx_h, _, _ = fixed_bits(gb, g, S, flags=gb.GBBC_HOST_LOOP)
+    fx_h, _, _ = fixed_bits(gb, g, S, device=False)
     assert st["wide_batches"] >= 1 and st["batches"] == 1 and st["sources"] == len(S)
     assert np.array_equal(fx_p, fx_h)
     want, _ = oracle.bc_graph(g, S)
@@ -77,11 +80,11 @@ def test_persistent_multi_graph_handle(gb):
         loc += list(s)
     gid, loc = np.array(gid, np.int32), np.array(loc, np.int32)
     outs = []
-    for flags in (0, gb.GBBC_HOST_LOOP):
+    for flags in (gb.GBBC_DEVICE_LOOP, 0):
         with gb.BC.from_graphs(graphs, schedule="grid", flags=flags) as bc:
             bc.compute_multi(gid, loc)
             outs.append(bc.read_fixed())
-            if flags == 0:
+            if flags:
                 per = [bc.read(graph_id=i) for i in range(len(graphs))]
     assert np.array_equal(outs[0], outs[1])
     for i, h in enumerate(graphs):
@@ -95,7 +98,7 @@ def test_timeout_spins_ends_the_launch_with_an_error(gb):
     # GBBC_ERR_TIMEOUT (a host-side status; the context stays usable)
     g = gg.rmat(14, 16, seed=331)
     S = gg.sample_sources(g.n, 256, seed=331)
-    with gb.BC.from_graph(g, schedule="grid", timeout_spins=1) as bc:
+    with gb.BC.from_graph(g, schedule="grid", timeout_spins=1, flags=gb.GBBC_DEVICE_LOOP) as bc:
         with pytest.raises(gb.GbbcError) as e:
             bc.compute(S)
         assert e.value.status == gb.GBBC_ERR_TIMEOUT
@@ -104,7 +107,7 @@ def test_timeout_spins_ends_the_launch_with_an_error(gb):
         assert np.all(bc.read() == 0)
     # the device is fine: a handle with the default bound gives the host
     # loop's bits
-    want_fx, _, _ = fixed_bits(gb, g, S, flags=gb.GBBC_HOST_LOOP)
+    want_fx, _, _ = fixed_bits(gb, g, S, device=False)
     got_fx, _, _ = fixed_bits(gb, g, S)
     assert np.array_equal(got_fx, want_fx)
 
@@ -112,7 +115,7 @@ def test_timeout_spins_ends_the_launch_with_an_error(gb):
 def test_persistent_launch_count(gb):
     g = gg.rmat(15, 16, seed=341)
     S = gg.sample_sources(g.n, 1024, seed=341)
-    with gb.BC.from_graph(g, schedule="grid") as bc:
+    with gb.BC.from_graph(g, schedule="grid", flags=gb.GBBC_DEVICE_LOOP) as bc:
         before = bc.stats()["kernel_launches"]
         bc.compute(S)
         launches = bc.stats()["kernel_launches"] - before
