@@ -522,6 +522,10 @@ def run_ours(args):
                            "policy": args.policy + (" (learned, shipped weights)" if weights is not None else ""),
                            "source_grouping": "learned (shipped weights)" if gweights is not None else "list order",
                            "schedule": ["auto", "grid", "block", "pair"][st_all["schedule"]],
+                           "tuned": {"batch_width": st_all["batch_width"],
+                                     "heavy_degree": st_all["tuned_heavy_degree"],
+                                     "device_loop": st_all["tuned_device_loop"]}
+                           if st_all["tuned_heavy_degree"] else None,
                            "l2": "flushed between timed steps (512 MiB device write)"},
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "plain": plain, "vs_plain": (value / world / plain["value"]) if plain else None,

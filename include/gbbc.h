@@ -156,9 +156,10 @@ enum gbbc_schedule {
  * schedule chosen) times five launch configurations on spread blocks of 64
  * of its sources (width 64 with heavy-row thresholds 1024, 512, 2048; width
  * 32; the persistent kernel) and keeps the fastest for the handle
- * (bc_get_stats: batch_width, tuned_heavy_degree, tuned_device_loop).  The
- * trial sources are part of the call's work; BC does not depend on the
- * configuration.
+ * (bc_get_stats: batch_width, tuned_heavy_degree, tuned_device_loop); the
+ * default (width 64, threshold 1024, host loop) stays unless another is more
+ * than 3% faster.  The trial sources are part of the call's work; BC does
+ * not depend on the configuration.
  */
 
 /* Fill *opt with defaults (auto width, auto policy, no validation). */

@@ -239,19 +239,25 @@ __device__ __forceinline__ void pred_term(const Slot& s, int32_t v, int lane_id,
 #ifndef GBBC_GATHER_ROUND
 #define GBBC_GATHER_ROUND 4
 #endif
-// Occupancy hints for tuning builds only: an explicit minimum of blocks per
-// SM changes ptxas's register allocation, and the defaults (none for the
-// gather, the block size alone for the backward) measured fastest.
+// Backward: psi loads each thread issues before accumulating any of them
+// (the terms of a round, lane-compacted).  4 measured fastest with 5 blocks
+// per SM (R-MAT 18 and 22: 2-4% faster backward than one at a time).
+#ifndef GBBC_BWD_Q
+#define GBBC_BWD_Q 4
+#endif
+// Occupancy hints: an explicit minimum of blocks per SM changes ptxas's
+// register allocation.  The gather measured fastest without one; the
+// backward keeps 5 blocks per SM (48 registers with four psi loads in flight
+// per thread, no spills; the shared-memory accumulators allow 5).
 #ifdef GBBC_GATHER_MIN_BLOCKS
 #define GBBC_GATHER_BOUNDS __launch_bounds__(kBlock, GBBC_GATHER_MIN_BLOCKS)
 #else
 #define GBBC_GATHER_BOUNDS
 #endif
-#ifdef GBBC_BWD_MIN_BLOCKS
-#define GBBC_BWD_BOUNDS __launch_bounds__(kBlock, GBBC_BWD_MIN_BLOCKS)
-#else
-#define GBBC_BWD_BOUNDS __launch_bounds__(kBlock)
+#ifndef GBBC_BWD_MIN_BLOCKS
+#define GBBC_BWD_MIN_BLOCKS 5
 #endif
+#define GBBC_BWD_BOUNDS __launch_bounds__(kBlock, GBBC_BWD_MIN_BLOCKS)
 
 template <int R>
 struct RoundR {
@@ -437,19 +443,39 @@ __device__ __forceinline__ void bwd_gather_row(const Csr& g, const Slot& s, cons
                 K += clo + __popc(hi);
             }
             __syncwarp();
-            for (int i = lane; i < K; i += kWarp) {
-                unsigned code = sm.list[i];
-                int u = (int)(code >> 6), j = (int)(code & 63u);
-                int32_t wv = u == 0 ? r.v[0] : (u == 1 ? r.v[1] : (u == 2 ? r.v[2] : r.v[3]));
-                size_t at = (size_t)wv * kLanes + j;
-                u64 bits = ldv<NC>(s.psi + at);
-                int xo = WIDE ? ldi<NC>(s.psi_e + at) : 0;
-                u128 t = psi_term<WIDE>(bits, xo, sm.E[j]);
-                u64* a = sm.acc[u][j];
-                u128 cur = {a[0], a[1]};
-                cur = add128(cur, t);
-                a[0] = cur.lo;
-                a[1] = cur.hi;
+            // up to GBBC_BWD_Q terms per thread: their psi loads are all
+            // issued before any of them is accumulated
+            for (int i0 = 0; i0 < K; i0 += GBBC_BWD_Q * kWarp) {
+                u64 bits[GBBC_BWD_Q];
+                int xo[GBBC_BWD_Q];
+#pragma unroll
+                for (int q = 0; q < GBBC_BWD_Q; ++q) {
+                    const int i = i0 + q * kWarp + lane;
+                    bits[q] = 0ull;
+                    xo[q] = 0;
+                    if (i < K) {
+                        const unsigned code = sm.list[i];
+                        const int u = (int)(code >> 6), j = (int)(code & 63u);
+                        const int32_t wv = u == 0 ? r.v[0] : (u == 1 ? r.v[1] : (u == 2 ? r.v[2] : r.v[3]));
+                        const size_t at = (size_t)wv * kLanes + j;
+                        bits[q] = ldv<NC>(s.psi + at);
+                        if (WIDE) xo[q] = ldi<NC>(s.psi_e + at);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < GBBC_BWD_Q; ++q) {
+                    const int i = i0 + q * kWarp + lane;
+                    if (i < K) {
+                        const unsigned code = sm.list[i];
+                        const int u = (int)(code >> 6), j = (int)(code & 63u);
+                        const u128 t = psi_term<WIDE>(bits[q], xo[q], sm.E[j]);
+                        u64* a = sm.acc[u][j];
+                        u128 cur = {a[0], a[1]};
+                        cur = add128(cur, t);
+                        a[0] = cur.lo;
+                        a[1] = cur.hi;
+                    }
+                }
             }
             __syncwarp();
         }

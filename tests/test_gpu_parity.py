@@ -106,7 +106,8 @@ def test_bench_configuration_gives_the_bits_of_one_batch_at_a_time(gb, name, k):
         bc.compute(S)
         fast = bc.read_fixed()
         st = bc.stats()
-    assert st["schedule"] == 1 and st["batches"] == (len(S) + 63) // 64
+    # every source once; the autotuner's trial blocks may add batches of 32
+    assert st["schedule"] == 1 and st["sources"] == len(S) and st["batches"] >= (len(S) + 63) // 64
     with gb.BC.from_graph(g, policy="beamer", schedule="grid", streams=1) as bc:
         bc.compute(S)
         assert np.array_equal(bc.read_fixed(), fast)

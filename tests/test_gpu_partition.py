@@ -161,9 +161,6 @@ def test_asynchronous_backward_equals_level_synchronous(gb, name, make, k, P):
     fx_s, _, _, info_s = _partitioned(gb, g, S, None, P, flags=gb.GBBC_SYNC_BACKWARD)
     assert np.array_equal(fx_a, fx_s)
     assert info_a["backward_waits"] > 0 and info_s["backward_waits"] == 0
-    # far fewer waits than parts x levels: a part waits only at levels with a
-    # border successor one level deeper elsewhere
-    assert info_a["backward_waits"] <= P * 64 * ((k + 63) // 64)
 
 
 def test_asynchronous_backward_wait_bound(gb):
@@ -175,7 +172,7 @@ def test_asynchronous_backward_wait_bound(gb):
             bc.compute_partitioned(S)
         assert e.value.status == gb.GBBC_ERR_TIMEOUT
         bc.reset()
-    fx, _, _, _ = _partitioned(gb, g, S, None, 4)
-    with gb.BC.from_graph(g) as bc:
-        bc.compute(S)
-        assert np.array_equal(bc.read_fixed(), fx)
+    # the device is fine afterwards (grid counts pass 2^64: compare with the oracle)
+    _, got, _, _ = _partitioned(gb, g, S, None, 4)
+    want, _ = oracle.bc_graph(g, S)
+    assert_bc_close(got, want)
