@@ -15,8 +15,9 @@ events on the compute stream.
 Beside the headline the line carries:
   plain      the plain one-source-at-a-time GPU Brandes (batch width 1,
              the same handle options) on a seeded sample of the list, timed
-             the same way, with the batched form on the same sample;
-             vs_plain = value / plain.value
+             the same way; beside it the same sample with one source per
+             thread block, many blocks at once (plain.concurrent), and the
+             batched form on the sample; vs_plain = value / plain.value
   traversed  GTEPS counting only the edges each source's BFS reaches (the
              CSR entries of its connected component)
   e2e        the same metric through the C ABI with host buffers:
@@ -98,6 +99,9 @@ def parse():
                     help="sources of the single-core oracle sample (0: sized from the graph, about 10-30 s)")
     ap.add_argument("--plain-sources", type=int, default=256,
                     help="sources of the plain one-source-at-a-time arm's seeded sample (0: no plain arm)")
+    ap.add_argument("--plain-concurrent-sources", type=int, default=1216,
+                    help="sources of the one-source-per-thread-block plain arm's sample (two waves of the "
+                         "resident blocks on a 152-SM GPU)")
     return ap.parse_args()
 
 
@@ -406,9 +410,21 @@ def run_ours(args):
         p_steps = max(1, min(args.steps, 3))
         with make(rp, col, None, **dict(opts, batch_width=1)) as hp:
             ms_plain = timed(hp, sp, p_steps, 1)
+        # one source per thread block needs many more sources than resident
+        # blocks before it fills the GPU: its own, larger sample
+        kc = min(max(args.plain_concurrent_sources, kp), k)
+        sc = torch.from_numpy(gg.sample_sources(k, kc, seed=4243)).to(dev)
+        sc = src[sc.long()].contiguous()
+        with make(rp, col, None, **dict(opts, batch_width=1, schedule="block")) as hp:
+            ms_conc = timed(hp, sc, 1, 1)
         ms_batched = timed(bc, sp, p_steps, 1)
         plain = {"value": kp * g.nnz / (ms_plain / 1e3) / 1e9, "unit": UNIT, "sources": kp, "steps": p_steps,
                  "ms_per_step": ms_plain, "sample": "seeded uniform sample (seed 4242) of the source list",
+                 "concurrent": {"value": kc * g.nnz / (ms_conc / 1e3) / 1e9, "ms_per_step": ms_conc,
+                                "sources": kc, "steps": 1,
+                                "sample": "seeded uniform sample (seed 4243) of the source list",
+                                "design": "one source per thread block, many blocks at once "
+                                          "(batch width 1, block schedule)"},
                  "batched_on_sample": {"value": kp * g.nnz / (ms_batched / 1e3) / 1e9, "ms_per_step": ms_batched}}
 
     # ---- end to end through the C ABI with host buffers ----

@@ -85,7 +85,9 @@ typedef struct gbbc_options {
     uint32_t struct_size;  /* sizeof(gbbc_options); set by bc_options_init */
     int32_t batch_width;   /* sources per bitset word: 0 = automatic (64, or
                               tuned; see autotuning), 1 = plain
-                              one-source-at-a-time kernels, 32 or 64 */
+                              one-source-at-a-time kernels (with
+                              GBBC_SCHEDULE_BLOCK: one source per thread
+                              block, many blocks at once), 32 or 64 */
     int32_t policy;        /* enum gbbc_policy */
     int32_t validate;      /* 1: check CSR symmetry, sorted rows, no loops or
                               duplicates on the device at create time */
@@ -137,7 +139,17 @@ enum gbbc_schedule {
     GBBC_SCHEDULE_BLOCK = 2, /* one thread-block cluster (1 to 8 blocks) per
                                 batch, many batches at once, one persistent
                                 launch per call; the level loop runs on the
-                                device (cluster barriers only) */
+                                device (cluster barriers only).  With
+                                batch_width 1: each thread block runs whole
+                                sources from the call's list, one at a time,
+                                on per-block arrays of 28n bytes (as many
+                                blocks as fit in half the free memory and
+                                mem_limit_bytes, at most the resident count);
+                                BC bits equal the other paths'; kept state and
+                                tracing use the one-source-at-a-time kernels.
+                                A source whose counts reach 2^64 adds nothing
+                                and the call fails with GBBC_ERR_CAPACITY
+                                after the other sources were added */
     GBBC_SCHEDULE_PAIR = 3   /* the weighted graphs' kernel with all weights
                                 1: one block per batch of ceil(k / resident
                                 blocks) sources (at most 64), work items

@@ -22,6 +22,7 @@
 
 #include "bc_fixed.cuh"
 #include "bc_internal.cuh"
+#include "bc_plain.cuh"
 
 using namespace gbbc;
 
@@ -64,6 +65,8 @@ struct gbbc_graph {
     bool slot_ready = false;
     PlainState plain;            // batch width 1
     bool plain_ready = false;
+    PlainBlocks pblk;            // batch width 1 on the block schedule: a source per thread block
+    unsigned long long* d_pnext = nullptr;   // [4] work-list counter, then the kernel's stats
     gbbc_options opt;
     std::string err;
     std::vector<std::pair<void*, size_t>> allocs;
@@ -839,6 +842,73 @@ gbbc_status run_plain(gbbc_graph* g, int32_t src, int32_t lo, int32_t hi, long l
     return GBBC_OK;
 }
 
+// Batch width 1 on the block schedule: up to `want` thread blocks, each with
+// its own per-source arrays (28n + 8 bytes per block), as many as fit in half
+// of the free memory (and mem_limit_bytes).
+gbbc_status alloc_plain_blocks(gbbc_graph* g, int want) {
+    PlainBlocks& B = g->pblk;
+    if (B.count >= want) return GBBC_OK;
+    for (void* q : {(void*)B.dist, (void*)B.sigma, (void*)B.psi, (void*)B.queue, (void*)B.lev, (void*)B.ctr})
+        dfree(g, q);
+    B = PlainBlocks();
+    const size_t n = (size_t)std::max<int32_t>(g->n, 1);
+    if (!g->d_pnext) CKS(dalloc_t(g, &g->d_pnext, 4));
+    const double per_block = (double)n * 28.0 + 8.0 + sizeof(Counters);
+    double budget = 0.5 * (double)avail_bytes(g->device);
+    if (g->opt.mem_limit_bytes > 0) budget = std::min(budget, (double)g->opt.mem_limit_bytes - (double)g->bytes);
+    const int count = (int)std::min<double>((double)want, std::floor(budget / per_block));
+    if (count < 1) return fail(g, GBBC_ERR_OOM, "no room for one plain-path block state (%.0f bytes)", per_block);
+    const size_t c = (size_t)count;
+    B.n = g->n;
+    CKS(dalloc_t(g, &B.dist, c * n));
+    CKS(dalloc_t(g, &B.sigma, c * n));
+    CKS(dalloc_t(g, &B.psi, c * n));
+    CKS(dalloc_t(g, &B.queue, c * n));
+    CKS(dalloc_t(g, &B.lev, c * (n + 2)));
+    CKS(dalloc_t(g, &B.ctr, c));
+    B.count = count;
+    return GBBC_OK;
+}
+
+// Batch width 1, block schedule: every source runs whole on one thread block
+// (McLaughlin and Bader's coarse-grained source parallelism), many blocks at
+// once, one launch per call.  BC bits equal those of the other paths.
+gbbc_status run_plain_blocks(gbbc_graph* g, const std::vector<int32_t>& gsrc, cudaStream_t st) {
+    const long long k = (long long)gsrc.size();
+    if (k == 0) return GBBC_OK;
+    const int bps = plain_blocks_per_sm();
+    if (bps < 1) return fail(g, GBBC_ERR_CUDA, "plain block kernel: no resident block");
+    if (g->d_bsrc_cap < k) {
+        dfree(g, g->d_bsrc);
+        CKS(dalloc_t(g, &g->d_bsrc, (size_t)k));
+        g->d_bsrc_cap = k;
+    }
+    CKS(alloc_plain_blocks(g, (int)std::min<long long>(k, (long long)g->nsm * bps)));
+    PlainBlocks& B = g->pblk;
+    const size_t n = (size_t)std::max<int32_t>(g->n, 1), c = (size_t)B.count;
+    CK(g, cudaMemcpyAsync(g->d_bsrc, gsrc.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(g, cudaMemsetAsync(B.dist, 0xff, c * n * sizeof(int32_t), st));
+    CK(g, cudaMemsetAsync(B.sigma, 0, c * n * sizeof(u64), st));
+    CK(g, cudaMemsetAsync(B.ctr, 0, c * sizeof(Counters), st));
+    CK(g, cudaMemsetAsync(g->d_pnext, 0, 4 * sizeof(unsigned long long), st));
+    Csr cs{g->n, g->nnz, g->d_row_ptr, g->d_col};
+    CK(g, launch_plain_blocks(cs, B, g->d_bsrc, k, g->d_pnext, g->d_bc, g->d_pnext + 1, st));
+    g->stats.kernel_launches++;
+    unsigned long long h[4];
+    CK(g, cudaMemcpyAsync(h, g->d_pnext, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(g, cudaStreamSynchronize(st));
+    if ((long long)h[1] != k) return fail(g, GBBC_ERR_CUDA, "plain block kernel ran %llu of %lld sources", h[1], k);
+    g->stats.batches += k;
+    g->stats.sources += k;
+    g->stats.levels_fwd += (long long)h[2];
+    g->stats.levels_push += (long long)h[2];
+    g->stats.schedule = GBBC_SCHEDULE_BLOCK;
+    if (h[3] & 0xffffffffull)
+        return fail(g, GBBC_ERR_CAPACITY,
+                    "plain path (batch width 1): a shortest-path count reached 2^64; use batch width 32 or 64");
+    return GBBC_OK;
+}
+
 gbbc_status alloc_keep(gbbc_graph* g, long long k, cudaStream_t st) {
     dfree(g, g->k_dist);
     dfree(g, g->k_sigma);
@@ -1335,6 +1405,8 @@ gbbc_status compute_batched(gbbc_graph* g, const std::vector<int32_t>& gsrc, con
                             cudaStream_t st, bool mixed) {
     long long k = (long long)gsrc.size();
     if (g->opt.batch_width == 1) {  // plain: one source at a time, list order
+        if (g->opt.schedule == GBBC_SCHEDULE_BLOCK && !g->k_dist && !(g->opt.flags & GBBC_TRACE))
+            return run_plain_blocks(g, gsrc, st);
         CKS(alloc_plain(g));
         for (long long i = 0; i < k; ++i)
             CKS(run_plain(g, gsrc[i], (int32_t)g->goff[gid[i]], (int32_t)g->goff[gid[i] + 1], i, st));

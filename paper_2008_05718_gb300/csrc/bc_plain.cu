@@ -12,11 +12,18 @@
 //              batched path (bc_fixed.cuh), so both give identical BC bits.
 // Counts of 2^64 or more are not supported here (GBBC_ERR_CAPACITY); the
 // batched path handles them.
+//
+// The same steps also run with coarse-grained source parallelism (the block
+// schedule with batch width 1, McLaughlin and Bader's design): every thread
+// block runs whole sources one after another, taken from a work list, on
+// its own per-source arrays; many blocks run at once.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "bc_fixed.cuh"
 #include "bc_internal.cuh"
+#include "bc_plain.cuh"
+#include "bc_rows.cuh"
 
 namespace gbbc {
 
@@ -186,6 +193,123 @@ void launch_plain_bwd(const Csr& g, const PlainState& p, u64* bc, long long q_lo
     if (q_hi <= q_lo) return;
     k_plain_bwd<<<plain_grid(q_hi - q_lo, nsm), kBlock, 0, st>>>(g, p, bc, q_lo, q_hi, level, heavy_deg);
     k_plain_bwd_heavy<<<nsm * 2, kHeavyBlock, 0, st>>>(g, p, bc, level);
+}
+
+// ---- one source per thread block, many blocks at once -------------------
+// Block b owns dist/sigma/psi/queue rows b of the PlainBlocks arrays (clean
+// between sources: dist -1 and sigma 0 everywhere), and level boundaries.
+// Inside the block a warp takes each frontier vertex (whole rows, however
+// long); the levels are separated by block barriers.  After the backward the
+// block resets dist and sigma of the vertices it reached.  BC is added with
+// exact 128-bit atomics: blocks may add into one vertex at the same time.
+__global__ void __launch_bounds__(kPlainBlock) k_plain_blocks(Csr g, PlainBlocks B, const int32_t* src, long long k,
+                                                             unsigned long long* next, u64* bc,
+                                                             unsigned long long* stats) {
+    __shared__ long long s_i;
+    __shared__ long long s_hi;
+    __shared__ unsigned s_carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const size_t n = (size_t)B.n;
+    PlainState p;
+    p.n = B.n;
+    p.dist = B.dist + blockIdx.x * n;
+    p.sigma = B.sigma + blockIdx.x * n;
+    p.psi = B.psi + blockIdx.x * n;
+    p.queue = B.queue + blockIdx.x * n;
+    p.heavy = nullptr;
+    p.ctr = B.ctr + blockIdx.x;
+    int32_t* lev = B.lev + blockIdx.x * (n + 2);
+    for (;;) {
+        if (threadIdx.x == 0) s_i = (long long)atomicAdd(next, 1ull);
+        __syncthreads();
+        const long long i = s_i;
+        if (i >= k) break;
+        const int32_t s0 = src[i];
+        if (threadIdx.x == 0) {
+            p.dist[s0] = 0;
+            p.sigma[s0] = 1ull;
+            p.queue[0] = s0;
+            p.ctr->qtail = 1ull;
+            lev[0] = 0;
+            lev[1] = 1;
+        }
+        __syncthreads();
+        int level = 0;
+        for (;;) {  // forward, level by level
+            const long long q_lo = lev[level], q_hi = lev[level + 1];
+            for (long long e = q_lo + wid; e < q_hi; e += nw) {
+                const int32_t v = p.queue[e];
+                plain_push_row(g, p, v, level, __ldg(g.row_ptr + v), __ldg(g.row_ptr + v + 1), lane, kWarp);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_hi = (long long)(*(volatile unsigned long long*)&p.ctr->qtail);
+                lev[level + 2] = (int32_t)s_hi;
+                s_carry = *(volatile unsigned*)&p.ctr->carry;
+            }
+            __syncthreads();
+            if (s_hi == q_hi) break;
+            ++level;
+        }
+        const int nlev = level + 1;
+        // backward, levels nlev-1 .. 1; skipped for a source whose counts
+        // reached 2^64 (the call then fails with nothing of it added)
+        for (int l = s_carry ? 0 : nlev - 1; l >= 1; --l) {
+            for (long long e = lev[l] + wid; e < lev[l + 1]; e += nw) {
+                const int32_t v = p.queue[e];
+                const int Ev = 63 - __clzll(p.sigma[v]);
+                u128 a = plain_bwd_row(g, p, l, Ev, __ldg(g.row_ptr + v), __ldg(g.row_ptr + v + 1), lane, kWarp);
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) {
+                    u128 x = {__shfl_xor_sync(PFULL, a.lo, o), __shfl_xor_sync(PFULL, a.hi, o)};
+                    a = add128(a, x);
+                }
+                if (lane == 0) {
+                    const u64 x = p.sigma[v];
+                    const int lz = __clzll(x);
+                    const u64 N = x << lz;
+                    const u128 d = mul_shift63(N, a);
+                    u128 psi = add128(recip127(N), a);
+                    u64 M;
+                    int ex;
+                    round128(psi, -64 - (63 - lz), M, ex);
+                    p.psi[v] = double_bits(M, ex);
+                    atomic_add128(bc + 2 * (size_t)v, d);
+                }
+            }
+            __syncthreads();
+        }
+        // reset what this source touched; report counts of 2^64 or more
+        const long long reached = lev[nlev];
+        for (long long e = threadIdx.x; e < reached; e += blockDim.x) {
+            const int32_t v = p.queue[e];
+            p.dist[v] = -1;
+            p.sigma[v] = 0ull;
+        }
+        if (threadIdx.x == 0) {
+            atomicAdd(stats, 1ull);
+            atomicAdd(stats + 1, (unsigned long long)nlev);
+            if (s_carry) atomicOr((unsigned*)(stats + 2), 1u);
+            p.ctr->carry = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+int plain_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plain_blocks, kPlainBlock, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t launch_plain_blocks(const Csr& g, const PlainBlocks& B, const int32_t* src, long long k,
+                                unsigned long long* next, u64* bc, unsigned long long* stats, cudaStream_t st) {
+    if (k <= 0 || B.count < 1) return cudaSuccess;
+    k_plain_blocks<<<B.count, kPlainBlock, 0, st>>>(g, B, src, k, next, bc, stats);
+    return cudaGetLastError();
 }
 
 }  // namespace gbbc

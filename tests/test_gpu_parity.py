@@ -319,6 +319,48 @@ def test_plain_path_rejects_wide_counts(gb):
         assert e.value.status == gb.GBBC_ERR_CAPACITY
 
 
+# ---- batch width 1 on the block schedule: a source per thread block ----------
+
+PLAIN_BLOCK_CASES = [
+    ("er4096", lambda: gg.workload("er4096")[0], 300, 0),  # every source on a block of its own
+    ("rmat14", lambda: gg.rmat(14, 16, seed=24), 700, 0),  # more sources than resident blocks
+    ("rmat12_few_blocks", lambda: gg.rmat(12, 16, seed=25), 257, 2 << 20),  # a dozen blocks: many sources each
+    ("components", lambda: gg.from_edges(9, [(0, 1), (1, 2), (4, 5), (5, 6), (6, 4)]), 9, 0),
+]
+
+
+@pytest.mark.parametrize("name,make,k,limit", PLAIN_BLOCK_CASES, ids=[c[0] for c in PLAIN_BLOCK_CASES])
+def test_plain_blocks_parity_and_identical_bits(gb, name, make, k, limit):
+    g = make()
+    S = gg.sample_sources(g.n, min(g.n, k), seed=24)
+    opts = {"mem_limit_bytes": limit} if limit else {}
+    with gb.BC.from_graph(g, batch_width=1, schedule="block", **opts) as bc:
+        bc.compute(S)
+        fx, got, st = bc.read_fixed(), bc.read(), bc.stats()
+    assert st["sources"] == len(S) and st["schedule"] == gb.SCHEDULE["block"]
+    want, _ = oracle.bc_graph(g, S)
+    assert_bc_close(got, want)
+    with gb.BC.from_graph(g, batch_width=64) as bc:
+        bc.compute(S)
+        assert np.array_equal(fx, bc.read_fixed())  # same integer sums, same bits
+
+
+def test_plain_blocks_multi_graph_and_wide_counts(gb):
+    graphs = [gg.rmat(10, 8, seed=26), gg.cycle(50), gg.full_grid(6, 7)]
+    gid = np.repeat(np.arange(3, dtype=np.int32), 40)
+    local = np.concatenate([gg.sample_sources(h.n, 40, seed=27 + i) for i, h in enumerate(graphs)]).astype(np.int32)
+    out = []
+    for opts in ({"batch_width": 1, "schedule": "block"}, {"batch_width": 64}):
+        with gb.BC.from_graphs(graphs, **opts) as bc:
+            bc.compute_multi(gid, local)
+            out.append(bc.read_fixed())
+    assert np.array_equal(out[0], out[1])
+    with gb.BC.from_graph(gg.diamond_chain(70), batch_width=1, schedule="block") as bc:
+        with pytest.raises(gb.GbbcError) as e:
+            bc.compute([0, 1])
+        assert e.value.status == gb.GBBC_ERR_CAPACITY
+
+
 # ---- the block-per-batch schedule and the autotuner --------------------------
 
 @pytest.mark.parametrize("make,k", [(lambda: gg.workload("er4096")[0], 300), (lambda: gg.rmat(12, 16, seed=61), 300),
