@@ -7,6 +7,12 @@ about half an hour on 8 cores), so it runs offline in three steps:
     python tests/full_size_check.py gpu     --workload rmat22 --out gpu_bc.npy
     python tests/full_size_check.py compare oracle_bc.npy gpu_bc.npy
 
+The oracle step can be split: `oracle --part K/N` covers the K-th of N
+contiguous slices of the source list (K = 0 .. N-1), so that the slices can
+run on different machines or at different times, and
+`sum --out oracle_bc.npy part0.npy part1.npy ...` adds the slices' BC
+vectors in the order given.
+
 `oracle` runs the plain CPU oracle over every source of the workload, in
 worker processes (oracle/pool.py); `gpu` runs the CUDA library through the
 C ABI in the benchmark's launch configuration (shipped direction and
@@ -39,11 +45,26 @@ def _workload(name):
 def run_oracle(args):
     from oracle.pool import OraclePool
     g, S = _workload(args.workload)
+    part = "0/1"
+    if args.part:
+        k, n = (int(x) for x in args.part.split("/"))
+        assert 0 <= k < n, args.part
+        S = np.array_split(S, n)[k]
+        part = args.part
     with OraclePool(g, procs=args.procs) as pool:
         bc, dt = pool.bc(S, shares_per_proc=4)
     np.save(args.out, bc)
-    print(json.dumps({"workload": args.workload, "sources": len(S), "n": g.n, "nnz": g.nnz,
+    print(json.dumps({"workload": args.workload, "part": part, "sources": len(S), "n": g.n, "nnz": g.nnz,
                       "procs": pool.procs, "seconds": round(dt, 1), "out": args.out}))
+
+
+def run_sum(args):
+    total = None
+    for path in args.parts:
+        x = np.load(path)
+        total = x.copy() if total is None else total + x
+    np.save(args.out, total)
+    print(json.dumps({"parts": len(args.parts), "out": args.out}))
 
 
 def run_gpu(args):
@@ -93,6 +114,10 @@ def main():
     a.add_argument("--workload", default="rmat22")
     a.add_argument("--out", required=True)
     a.add_argument("--procs", type=int, default=None)
+    a.add_argument("--part", default=None, help="K/N: the K-th of N contiguous slices of the source list")
+    d = sub.add_parser("sum")
+    d.add_argument("--out", required=True)
+    d.add_argument("parts", nargs="+")
     b = sub.add_parser("gpu")
     b.add_argument("--workload", default="rmat22")
     b.add_argument("--out", required=True)
@@ -104,6 +129,8 @@ def main():
         return run_oracle(args)
     if args.cmd == "gpu":
         return run_gpu(args)
+    if args.cmd == "sum":
+        return run_sum(args)
     return run_compare(args)
 
 
