@@ -657,12 +657,10 @@ __device__ bool block_batch(const Csr& g, const Slot& s, long long* lev, unsigne
                 u64 N0, N1;
                 int E0, E1;
                 lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
-                u128 a0, a1;
-                bwd_row_begin(sm, E0, E1);
+                bwd_row_begin_n(sm, N0, E0, N1, E1);
                 bwd_gather_row<1, WIDE, false>(g, s, Fs, l, m, __ldg(g.row_ptr + v), __ldg(g.row_ptr + v + 1), 0,
                                                sm);
-                bwd_row_end(sm, a0, a1);
-                bwd_store<WIDE, true>(s, bc, v, m, E0, E1, N0, N1, a0, a1);
+                bwd_row_finish<WIDE, true>(s, bc, v, m, sm);
             }
         }
         csync();

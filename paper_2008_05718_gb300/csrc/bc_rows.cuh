@@ -240,7 +240,7 @@ __device__ __forceinline__ void pred_term(const Slot& s, int32_t v, int lane_id,
 #define GBBC_GATHER_ROUND 4
 #endif
 // Backward: psi loads each thread issues before accumulating any of them
-// (the terms of a round, lane-compacted).  4 measured fastest with 5 blocks
+// (the terms of a flush, lane-compacted).  4 measured fastest with 5 blocks
 // per SM (R-MAT 18 and 22: 2-4% faster backward than one at a time).
 #ifndef GBBC_BWD_Q
 #define GBBC_BWD_Q 4
@@ -248,7 +248,7 @@ __device__ __forceinline__ void pred_term(const Slot& s, int32_t v, int lane_id,
 // Occupancy hints: an explicit minimum of blocks per SM changes ptxas's
 // register allocation.  The gather measured fastest without one; the
 // backward keeps 5 blocks per SM (48 registers with four psi loads in flight
-// per thread, no spills; the shared-memory accumulators allow 5).
+// per thread, no spills; its per-warp shared memory is 2.9 KB).
 #ifdef GBBC_GATHER_MIN_BLOCKS
 #define GBBC_GATHER_BOUNDS __launch_bounds__(kBlock, GBBC_GATHER_MIN_BLOCKS)
 #else
@@ -403,17 +403,59 @@ __device__ __forceinline__ u128 psi_term(u64 bits, int eoff, int Ev) {
     return shl_term(M, e + Ev + 12);
 }
 
-// Lane-compacted accumulation.  A round of up to four contributing
-// successors (slot u = 0..3, lanes f_u) is expanded into a list of
-// (slot, lane) terms, and each thread of the warp takes one term: it loads
-// psi[w_u][lane], shifts it to the lane's fixed point and adds it into
-// acc[u][lane] in shared memory.  Lanes are distinct within a slot, so the
-// adds need no atomics; the four slots are summed when the row is done.
+// Lane-compacted accumulation over a whole row chunk.  The chunk's
+// contributing successors (at most 32) get slots 0..S-1 in ballot order;
+// their (slot, lane) terms are listed slot by slot, and each thread of the
+// warp takes one term at a time: it loads psi[w_slot][lane], shifts it to
+// the lane's fixed point and adds it into the lane's accumulator in shared
+// memory.  Two terms of one flush may share a lane, so the adds are shared-
+// memory atomics; the 128-bit term is split into three parts (bits 0-31,
+// 32-63 and 64-127), each summed in its own 64-bit word, which cannot wrap
+// for fewer than 2^32 terms, and recombined when the row is done.  Integer
+// adds commute, so the sums do not depend on the order of the terms.
+constexpr int kBwdListCap = 256;  // terms per flush (at most 64 per successor)
 struct BwdWarpSmem {
-    u64 acc[4][kLanes][2];
+    u64 acc[kLanes][3];
+    u64 N[kLanes];
     int E[kLanes];
-    unsigned char list[4 * kLanes];
+    int32_t w[kWarp];
+    unsigned short list[kBwdListCap];
 };
+
+template <bool WIDE, bool NC>
+__device__ __forceinline__ void bwd_flush(const Slot& s, BwdWarpSmem& sm, int K) {
+    const int lane = threadIdx.x & 31;
+    for (int i0 = 0; i0 < K; i0 += GBBC_BWD_Q * kWarp) {
+        u64 bits[GBBC_BWD_Q];
+        int xo[GBBC_BWD_Q], jj[GBBC_BWD_Q];
+        // every psi load of the round is issued before any is used
+#pragma unroll
+        for (int q = 0; q < GBBC_BWD_Q; ++q) {
+            const int i = i0 + q * kWarp + lane;
+            bits[q] = 0ull;
+            xo[q] = 0;
+            jj[q] = -1;
+            if (i < K) {
+                const unsigned code = sm.list[i];
+                const int j = (int)(code & 63u);
+                const size_t at = (size_t)sm.w[code >> 6] * kLanes + j;
+                jj[q] = j;
+                bits[q] = ldv<NC>(s.psi + at);
+                if (WIDE) xo[q] = ldi<NC>(s.psi_e + at);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < GBBC_BWD_Q; ++q) {
+            if (jj[q] >= 0) {
+                const u128 t = psi_term<WIDE>(bits[q], xo[q], sm.E[jj[q]]);
+                u64* a = sm.acc[jj[q]];
+                atomicAdd(a, t.lo & 0xFFFFFFFFull);
+                atomicAdd(a + 1, t.lo >> 32);
+                if (t.hi) atomicAdd(a + 2, t.hi);
+            }
+        }
+    }
+}
 
 template <int NT, bool WIDE, bool NC = true>
 __device__ __forceinline__ void bwd_gather_row(const Csr& g, const Slot& s, const MaskTag* Fs, int level, u64 m,
@@ -430,60 +472,32 @@ __device__ __forceinline__ void bwd_gather_row(const Csr& g, const Slot& s, cons
             if (t.tag == level + 1) f = t.mask & m;
         }
         unsigned bal = __ballot_sync(FULL, f != 0);
+        if (!bal) continue;
+        if (f) sm.w[__popc(bal & below)] = w;
+        int K = 0, slot = 0;
         while (bal) {
-            Round4 r;
-            take_round<4>(bal, w, f, r);
-            int K = 0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                unsigned lo = (unsigned)r.f[u], hi = (unsigned)(r.f[u] >> 32);
-                int clo = __popc(lo);
-                if ((lo >> lane) & 1u) sm.list[K + __popc(lo & below)] = (unsigned char)((u << 6) | lane);
-                if ((hi >> lane) & 1u) sm.list[K + clo + __popc(hi & below)] = (unsigned char)((u << 6) | (lane + 32));
-                K += clo + __popc(hi);
+            const int src = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const u64 ff = shfl64(f, src);
+            const unsigned lo = (unsigned)ff, hi = (unsigned)(ff >> 32);
+            const int clo = __popc(lo);
+            if ((lo >> lane) & 1u) sm.list[K + __popc(lo & below)] = (unsigned short)((slot << 6) | lane);
+            if ((hi >> lane) & 1u)
+                sm.list[K + clo + __popc(hi & below)] = (unsigned short)((slot << 6) | (lane + 32));
+            K += clo + __popc(hi);
+            ++slot;
+            if (bal == 0 || K > kBwdListCap - kLanes) {
+                __syncwarp();
+                bwd_flush<WIDE, NC>(s, sm, K);
+                __syncwarp();
+                K = 0;
             }
-            __syncwarp();
-            // up to GBBC_BWD_Q terms per thread: their psi loads are all
-            // issued before any of them is accumulated
-            for (int i0 = 0; i0 < K; i0 += GBBC_BWD_Q * kWarp) {
-                u64 bits[GBBC_BWD_Q];
-                int xo[GBBC_BWD_Q];
-#pragma unroll
-                for (int q = 0; q < GBBC_BWD_Q; ++q) {
-                    const int i = i0 + q * kWarp + lane;
-                    bits[q] = 0ull;
-                    xo[q] = 0;
-                    if (i < K) {
-                        const unsigned code = sm.list[i];
-                        const int u = (int)(code >> 6), j = (int)(code & 63u);
-                        const int32_t wv = u == 0 ? r.v[0] : (u == 1 ? r.v[1] : (u == 2 ? r.v[2] : r.v[3]));
-                        const size_t at = (size_t)wv * kLanes + j;
-                        bits[q] = ldv<NC>(s.psi + at);
-                        if (WIDE) xo[q] = ldi<NC>(s.psi_e + at);
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < GBBC_BWD_Q; ++q) {
-                    const int i = i0 + q * kWarp + lane;
-                    if (i < K) {
-                        const unsigned code = sm.list[i];
-                        const int u = (int)(code >> 6), j = (int)(code & 63u);
-                        const u128 t = psi_term<WIDE>(bits[q], xo[q], sm.E[j]);
-                        u64* a = sm.acc[u][j];
-                        u128 cur = {a[0], a[1]};
-                        cur = add128(cur, t);
-                        a[0] = cur.lo;
-                        a[1] = cur.hi;
-                    }
-                }
-            }
-            __syncwarp();
         }
     }
 }
 
 // Before a row: publish the lanes' exponents.  After it: the lanes' sums
-// (slots added) for this thread's two lanes, leaving the slots at zero.
+// for this thread's two lanes, leaving the accumulators at zero.
 __device__ __forceinline__ void bwd_row_begin(BwdWarpSmem& sm, int E0, int E1) {
     const int lane = threadIdx.x & 31;
     sm.E[lane] = E0;
@@ -491,28 +505,36 @@ __device__ __forceinline__ void bwd_row_begin(BwdWarpSmem& sm, int E0, int E1) {
     __syncwarp();
 }
 
+__device__ __forceinline__ void bwd_row_begin_n(BwdWarpSmem& sm, u64 N0, int E0, u64 N1, int E1) {
+    const int lane = threadIdx.x & 31;
+    sm.N[lane] = N0;
+    sm.N[lane + 32] = N1;
+    bwd_row_begin(sm, E0, E1);
+}
+
+__device__ __forceinline__ u128 bwd_take(u64* a) {
+    // a[0] + a[1] * 2^32 + a[2] * 2^64, mod 2^128
+    u128 r;
+    r.lo = a[0] + (a[1] << 32);
+    r.hi = a[2] + (a[1] >> 32) + (r.lo < a[0] ? 1ull : 0ull);
+    a[0] = a[1] = a[2] = 0ull;
+    return r;
+}
+
 __device__ __forceinline__ void bwd_row_end(BwdWarpSmem& sm, u128& a0, u128& a1) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
-    a0.lo = a0.hi = a1.lo = a1.hi = 0ull;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        u128 x = {sm.acc[u][lane][0], sm.acc[u][lane][1]};
-        u128 y = {sm.acc[u][lane + 32][0], sm.acc[u][lane + 32][1]};
-        a0 = add128(a0, x);
-        a1 = add128(a1, y);
-        sm.acc[u][lane][0] = sm.acc[u][lane][1] = 0ull;
-        sm.acc[u][lane + 32][0] = sm.acc[u][lane + 32][1] = 0ull;
-    }
+    a0 = bwd_take(sm.acc[lane]);
+    a1 = bwd_take(sm.acc[lane + 32]);
     __syncwarp();
 }
 
 __device__ __forceinline__ void bwd_smem_zero(BwdWarpSmem& sm) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        sm.acc[u][lane][0] = sm.acc[u][lane][1] = 0ull;
-        sm.acc[u][lane + 32][0] = sm.acc[u][lane + 32][1] = 0ull;
+    for (int c = 0; c < 3; ++c) {
+        sm.acc[lane][c] = 0ull;
+        sm.acc[lane + 32][c] = 0ull;
     }
     __syncwarp();
 }
@@ -574,6 +596,45 @@ __device__ __forceinline__ void bwd_store(const Slot& s, u64* bc, int32_t v, u64
             bc[2 * (size_t)v + 1] = b.hi;
         }
     }
+}
+
+// Finish a row (after bwd_row_begin_n and bwd_gather_row): the lanes of m
+// are compacted, so a thread finishes one lane (two past 32 lanes) instead
+// of two mostly idle ones; each lane's sum is taken from shared memory,
+// delta and psi_v computed (bwd_lane), and the lanes' deltas summed into
+// BC[v].
+template <bool WIDE, bool ATOMIC_BC>
+__device__ __forceinline__ void bwd_row_finish(const Slot& s, u64* bc, int32_t v, u64 m, BwdWarpSmem& sm) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const unsigned lo = (unsigned)m, hi = (unsigned)(m >> 32);
+    const int clo = __popc(lo), cnt = clo + __popc(hi);
+    __syncwarp();
+    if ((lo >> lane) & 1u) sm.list[__popc(lo & below)] = (unsigned short)lane;
+    if ((hi >> lane) & 1u) sm.list[clo + __popc(hi & below)] = (unsigned short)(lane + 32);
+    __syncwarp();
+    u128 c;
+    c.lo = c.hi = 0ull;
+    for (int i = lane; i < cnt; i += kWarp) {
+        const int j = sm.list[i];
+        const u128 A = bwd_take(sm.acc[j]);
+        c = add128(c, bwd_lane<WIDE>(s, v, j, sm.N[j], sm.E[j], A));
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) c = add128(c, shfl_xor128(c, o));
+    if (lane == 0) {
+        if (ATOMIC_BC) {
+            atomic_add128(bc + 2 * (size_t)v, c);
+        } else {
+            u128 b;
+            b.lo = bc[2 * (size_t)v];
+            b.hi = bc[2 * (size_t)v + 1];
+            b = add128(b, c);
+            bc[2 * (size_t)v] = b.lo;
+            bc[2 * (size_t)v + 1] = b.hi;
+        }
+    }
+    __syncwarp();
 }
 
 template <bool WIDE>
@@ -860,11 +921,9 @@ __device__ __forceinline__ void bwd_entry(const Csr& g, const Slot& s, u64* bc, 
     u64 N0, N1;
     int E0, E1;
     lane_norms<WIDE>(s, v, m, N0, E0, N1, E1);
-    u128 a0, a1;
-    bwd_row_begin(sm, E0, E1);
+    bwd_row_begin_n(sm, N0, E0, N1, E1);
     bwd_gather_row<1, WIDE, NC>(g, s, Fs, level, m, beg, end, 0, sm);
-    bwd_row_end(sm, a0, a1);
-    bwd_store<WIDE, ATOMIC_BC>(s, bc, v, m, E0, E1, N0, N1, a0, a1);
+    bwd_row_finish<WIDE, ATOMIC_BC>(s, bc, v, m, sm);
 }
 
 // Backward chunk task t of a heavy row (a block of NW warps): per-lane u128
