@@ -99,6 +99,12 @@ def parse():
                     help="sources of the single-core oracle sample (0: sized from the graph, about 10-30 s)")
     ap.add_argument("--plain-sources", type=int, default=256,
                     help="sources of the plain one-source-at-a-time arm's seeded sample (0: no plain arm)")
+    ap.add_argument("--sources", type=int, default=0,
+                    help="use the first K sources of the workload's list (0: all of them)")
+    ap.add_argument("--partitions", type=int, default=0,
+                    help="run the partitioned method (border matrices, refinement, relaxation, asynchronous "
+                         "backward) with this many contiguous parts instead of bc_compute (0: off); no plain arm "
+                         "and no traced roofline then")
     ap.add_argument("--plain-concurrent-sources", type=int, default=1216,
                     help="sources of the one-source-per-thread-block plain arm's sample (two waves of the "
                          "resident blocks on a 152-SM GPU)")
@@ -303,6 +309,8 @@ def run_ours(args):
     _build.build()
     gbbc.load()
     g, S, wts = load_workload(args.workload, rank)
+    if args.sources > 0:
+        S = S[:args.sources]
     k = len(S)
     stream = torch.cuda.current_stream(dev)
     rp = torch.from_numpy(g.row_ptr).to(dev)
@@ -335,13 +343,28 @@ def run_ours(args):
             return gbbc.BC.from_csr(g.n, rp_, col_, stream=stream, **kw)
         return gbbc.BC.from_weighted(g.n, rp_, col_, wt_, stream=stream, **kw)
 
+    P = args.partitions
+
+    def compute(h, sources):
+        if P > 0:
+            h.compute_partitioned(sources, stream=stream)
+        else:
+            h.compute(sources, stream=stream)
+
     bc = prepare(make(rp, col, wt, **opts))
+    t_part = None
+    if P > 0:  # once per graph, outside the timed region (border matrices)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bc.partition(None, P, stream=stream)
+        torch.cuda.synchronize()
+        t_part = time.perf_counter() - t0
     if world > 1:
         from paper_2008_05718_gb300 import multirank as mr
 
     def step():
         bc.reset()
-        bc.compute(src, stream=stream)
+        compute(bc, src)
         if world > 1:  # the exchange step: every rank ends with the whole BC
             mr.reduce_bc(bc, stream=stream, device=dev)
         bc.read(out, stream=stream)
@@ -403,7 +426,7 @@ def run_ours(args):
 
     # ---- the plain one-source-at-a-time GPU path on a seeded sample ----
     plain = None
-    if args.plain_sources > 0 and wts is None and args.width != 1:
+    if args.plain_sources > 0 and wts is None and args.width != 1 and P == 0:
         kp = min(args.plain_sources, k)
         sp = torch.from_numpy(gg.sample_sources(k, kp, seed=4242)).to(dev)
         sp = src[sp.long()].contiguous()  # a seeded sample of the list itself
@@ -439,7 +462,9 @@ def run_ours(args):
     for _ in range(e2e_steps):
         with make(rp_h, col_h, wt_h, **opts) as h:
             prepare(h)
-            h.compute(src_h, stream=stream)
+            if P > 0:
+                h.partition(None, P, stream=stream)
+            compute(h, src_h)
             h.read(out_h, stream=stream)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
@@ -449,7 +474,9 @@ def run_ours(args):
 
     # ---- roofline of the dominant step kind (one traced step) ----
     st_all = bc.stats()
-    if wts is None and st_all["schedule"] != 3:
+    if P > 0:
+        prof = None
+    elif wts is None and st_all["schedule"] != 3:
         with make(rp, col, None, **dict(opts, flags=opts["flags"] | gbbc.GBBC_TRACE)) as tb:
             prepare(tb)
             tb.compute(src, stream=stream)
@@ -462,11 +489,15 @@ def run_ours(args):
                          "bytes": pair_bytes_per_step(g.n, g.nnz, k, nb, wts is not None)}}
     peak, peak_src = measured_peaks()
     grouping_name = "learned" if gweights is not None else "list order"
+    if prof is None:
+        prof = {}
     total_ms = sum(v["ms"] for v in prof.values())
     step_bytes = sum(v["bytes"] for v in prof.values())
     steps_ctx = {x: {"ms": round(v["ms"], 3), "GBps": (v["bytes"] / v["ms"] / 1e6) if v["ms"] else 0.0,
                      "bytes": v["bytes"]} for x, v in prof.items()}
-    if p_launches > 0:
+    if P > 0:
+        roof = None  # the per-step trace covers bc_compute's step kinds only
+    elif p_launches > 0:
         # the persistent grid-schedule kernel runs every level step of every
         # batch: its algorithmic bytes per launch are the whole step's (every
         # step kind's compulsory bytes, from a traced run of the same
@@ -494,9 +525,10 @@ def run_ours(args):
                 "peak_source": f"{peak_src} hbm_gbs (copy)", "steps": steps_ctx}
     # the whole step in the timed region: every step kind's algorithmic bytes
     # over the timed step time
-    roof["timed_step"] = {"algorithmic_bytes": step_bytes, "ms": 1e3 * total_s / args.steps,
-                          "GBps": step_bytes / total_s * args.steps / 1e9,
-                          "frac": step_bytes / total_s * args.steps / 1e9 / peak}
+    if roof is not None:
+        roof["timed_step"] = {"algorithmic_bytes": step_bytes, "ms": 1e3 * total_s / args.steps,
+                              "GBps": step_bytes / total_s * args.steps / 1e9,
+                              "frac": step_bytes / total_s * args.steps / 1e9 / peak}
 
     # ---- N > 1: the reduced BC of a sub-list against one GPU, bit for bit ----
     mcheck = None
@@ -542,7 +574,12 @@ def run_ours(args):
                                      "heavy_degree": st_all["tuned_heavy_degree"],
                                      "device_loop": st_all["tuned_device_loop"]}
                            if st_all["tuned_heavy_degree"] else None,
-                           "l2": "flushed between timed steps (512 MiB device write)"},
+                           "source_sample": (f"the first {k} sources of the workload's list" if args.sources > 0
+                                             else None),
+                           "l2": "flushed between timed steps (512 MiB device write)",
+                           "partitions": ({"parts": P, "kind": "contiguous vertex ranges",
+                                           "border_matrices_s": round(t_part, 3),
+                                           **bc.partition_info()} if P > 0 else None)},
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "plain": plain, "vs_plain": (value / world / plain["value"]) if plain else None,
                 "traversed": traversed, "multi_gpu_check": mcheck, "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
